@@ -1,0 +1,340 @@
+"""Benchmark: aggregate walker-ns/day and pair interactions/s of the batched
+multiple-walker lambda-ABF step on the solvation-like workload (4096
+flexible 3-site waters + a 12-site neutral alchemical solute, 12 300 atoms,
+5 nm box, reaction field, r_c = 1.0 nm, 16 walkers in a vdW and a Coulomb
+stage of 100 bins each, 1 fs steps), synthetic seeded inputs.
+
+One bench step = one la_step_walkers call advancing every walker by
+--md-steps MD steps (each MD step runs every part of the path: BAOAB of
+atoms and lambda, neighbour-list rebuild when needed, pair forces with
+dU/dlambda, bonded terms, ABF fold and bias).  L2 is flushed between bench
+steps (a 256 MB write).  `value` is timed with CUDA events on the engine's
+stream with the state resident in HBM; `e2e` times the same work through
+the C ABI with the walker state uploaded from pinned host memory before and
+read back (state + ABF accumulators) after every bench step.
+
+--impl reference times the FP64 oracle (the plain CPU statement of the
+method) on this machine's host cores on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "aggregate walker-ns/day"
+UNIT = "walker-ns/day"
+FLOP_PER_PAIR = 38  # FP32 flops per in-cutoff LJ+RF pair, force only (FMA = 2)
+WORKLOAD = ("solvation-like: 4096 flexible 3-site waters + 12-site alchemical solute "
+            "(12300 atoms, 5 nm box, RF eps_rf=78, r_c=1.0 nm, skin 0.1 nm), 16 walkers "
+            "(8 vdW-stage on [0,0.5] + 8 Coulomb-stage on [0.5,1]), 100 bins per stage, dt=1 fs, 300 K")
+
+
+def workload():
+    from paper_2307_08006_gb300 import synth
+
+    spec = synth.water_box(4096, 12, seed=8007)
+    run = synth.water_run(seed=8007, walkers_per_stage=8, n_bins=100, n_full=200.0)
+    return spec, run
+
+
+def walker_ns_per_day(n_walkers, md_steps, dt_ps, seconds):
+    return n_walkers * md_steps * dt_ps * 1e-3 / seconds * 86400.0
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(steps=2):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of
+    the same workload (all 16 walkers, `steps` MD steps, OpenMP over walkers)."""
+    import oracle
+
+    spec, run = workload()
+    from paper_2307_08006_gb300 import synth
+
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    st = synth.initial_state(spec, run)
+    sim = oracle.Simulation(spec, run, st)  # includes one force evaluation (untimed)
+    t0 = time.perf_counter()
+    sim.run(steps)
+    dt = time.perf_counter() - t0
+    val = walker_ns_per_day(run.n_walkers, steps, run.dt, dt)
+    return dict(value=val, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"{run.n_walkers} walkers x {steps} MD steps of the same workload "
+                       f"(O(N^2) FP64, OpenMP over walkers), {dt:.2f} s"), dt
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps_total, secs_total = 0, 0.0
+    cb = None
+    for k in range(args.warmup + args.steps):
+        cbk, dt = cpu_baseline(steps=1)
+        if k >= args.warmup:
+            steps_total += 1
+            secs_total += dt
+            cb = cbk
+    spec, run = workload()
+    val = walker_ns_per_day(run.n_walkers, steps_total, run.dt, secs_total)
+    cb["value"] = val
+    line = dict(impl="reference", metric=METRIC, value=val, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * secs_total / max(steps_total, 1),
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD, walkers=run.n_walkers, atoms_per_walker=spec.n,
+                            md_steps_per_bench_step=1),
+                cpu_baseline=cb, e2e=dict(value=val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, dev_index=0):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["unavailable"])
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(dev_index)]
+        if not rows:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["unavailable"])
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=reasons, samples=len(rows))
+
+
+def flush_l2(buf):
+    buf.add_(1)  # 256 MB read + write, larger than the 129 MB L2
+
+
+def gpu_arm(args):
+    import torch
+
+    from paper_2307_08006_gb300 import labf, synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec, run = workload()
+    state = synth.initial_state(spec, run, seed=run.seed + 1000 * rank)
+    eng = labf.Engine([labf.SystemInput(spec, run, state)],
+                      options=dict(graph_steps=args.graph_steps, autotune=int(args.autotune)), device=local)
+    stream = torch.cuda.current_stream(dev)
+    md = args.md_steps
+    # settle the lattice start (untimed): 2 ps
+    eng.step(args.settle)
+    eng.sync()
+    # in-cutoff pairs per MD step (all walkers), counted at the settled state
+    pairs_n = pairs_a = 0
+    for w in range(eng.n_walkers):
+        r = eng.energy_forces(w, count_pairs=True, forces=False)
+        pairs_n += r["pairs_normal"]
+        pairs_a += r["pairs_alch"]
+    pairs_per_md = pairs_n + pairs_a
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def bench_step():
+        eng.step(md, stream)
+
+    for _ in range(args.warmup):
+        bench_step()
+        flush_l2(flush)
+    torch.cuda.synchronize()
+    launches0 = int(eng.stats()[2])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(os.path.join(args.out_dir, f"clocks_rank{rank}.csv"))
+    with clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            bench_step()
+            ev[k][1].record(stream)
+            flush_l2(flush)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist is not None:
+        dist.barrier()
+    launches = int(eng.stats()[2]) - launches0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    secs = ms * 1e-3
+    value = walker_ns_per_day(run.n_walkers * world, args.steps * md, run.dt, secs)
+    pair_rate = pairs_per_md * world * args.steps * md / secs
+
+    # ---- end to end through the C ABI with host buffers ----
+    n, W = spec.n, run.n_walkers
+    pin_x = [torch.empty((n, 3), dtype=torch.float32, pin_memory=True) for _ in range(W)]
+    pin_v = [torch.empty((n, 3), dtype=torch.float32, pin_memory=True) for _ in range(W)]
+    host = [eng.get_state(w) for w in range(W)]
+    for w in range(W):
+        pin_x[w].numpy()[:] = host[w]["x"]
+        pin_v[w].numpy()[:] = host[w]["v"]
+    lam = [h["lam"] for h in host]
+    plam = [h["plam"] for h in host]
+    h2d = W * (2 * n * 3 * 4 + 16)
+    d2h_state = W * (2 * n * 3 * 4 + 16)
+    nb = sum(s.n_bins for s in run.stages)
+    d2h = d2h_state + nb * (8 + 8 + 8)
+
+    def e2e_step():
+        for w in range(W):
+            eng.set_state(w, x=pin_x[w].numpy(), v=pin_v[w].numpy(), lam=lam[w], plam=plam[w])
+        eng.step(md, stream)
+        for k in range(len(run.stages)):
+            eng.read_abf(0, k)
+        for w in range(W):
+            st = eng.get_state(w)
+            pin_x[w].numpy()[:] = st["x"]
+            pin_v[w].numpy()[:] = st["v"]
+            lam[w], plam[w] = st["lam"], st["plam"]
+
+    e2e_steps = max(2, min(args.steps, 5))
+    e2e_step()
+    flush_l2(flush)
+    torch.cuda.synchronize()
+    te = 0.0
+    for _ in range(e2e_steps):
+        t0 = time.perf_counter()
+        e2e_step()
+        torch.cuda.synchronize()
+        te += time.perf_counter() - t0
+        flush_l2(flush)
+        torch.cuda.synchronize()
+    te_t = torch.tensor([te], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+    e2e_val = walker_ns_per_day(run.n_walkers * world, e2e_steps * md, run.dt, float(te_t.item()))
+
+    # ---- plain form (one walker per launch sequence, no graph), same engine ----
+    plain_md = max(10, md // 5)
+    torch.cuda.synchronize()
+    pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eng.step_plain(2, stream)
+    pa.record(stream)
+    eng.step_plain(plain_md, stream)
+    pb.record(stream)
+    torch.cuda.synchronize()
+    plain_val = walker_ns_per_day(run.n_walkers * world, plain_md, run.dt, pa.elapsed_time(pb) * 1e-3)
+
+    # ---- roofline of the dominant kernel (pair pass), events per kernel ----
+    kt = eng.time_kernels(args.profile_steps, stream)
+    pair_ms = kt["pairs"][0]
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tflops = n_sm * 128 * 2 * 2.070e9 / 1e12  # FP32 lanes x FMA x max SM clock
+    achieved = pairs_per_md * FLOP_PER_PAIR / (pair_ms * 1e-3) / 1e12
+    eng.sync()
+    csum = clk.summary(local)
+
+    if rank == 0:
+        cb = None
+        if world == 1 and not args.no_cpu_baseline:
+            cb, _ = cpu_baseline(steps=args.cpu_steps)
+        line = dict(
+            metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+            dtype="f32", data="synthetic",
+            config=dict(workload=WORKLOAD, walkers=run.n_walkers, atoms_per_walker=spec.n,
+                        md_steps_per_bench_step=md, l2="flushed between bench steps (256 MB write)",
+                        parallelism="replicas" if world > 1 else "1 GPU, walkers batched",
+                        launch=eng.autotune_report()),
+            pair_interactions_per_s=pair_rate,
+            in_cutoff_pairs_per_md_step=pairs_per_md,
+            plain_form=dict(value=plain_val, unit=UNIT, md_steps=plain_md,
+                            note="one walker per launch sequence, no CUDA graph"),
+            e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
+                     note="state upload (la_set_state) + la_step_walkers + la_read_abf + la_get_state, "
+                          "host<->device copies in the timed region"),
+            gpu_launches=launches,
+            roofline=dict(bound="alu", achieved=achieved, peak=peak_tflops, unit="TFLOP/s",
+                          frac=achieved / peak_tflops, traffic=None,
+                          kernel="k_pairs (normal + alchemical pairs)",
+                          pair_kernel_ms=pair_ms,
+                          peak_note=f"{n_sm} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+                          kernel_ms=dict((k, v[0]) for k, v in kt.items())),
+            clocks=csum,
+            wall_s=wall,
+        )
+        if cb is not None:
+            line["cpu_baseline"] = cb
+        print(json.dumps(line))
+    eng.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="labf", choices=["labf", "reference"])
+    ap.add_argument("--md-steps", type=int, default=200)
+    ap.add_argument("--graph-steps", type=int, default=20)
+    ap.add_argument("--settle", type=int, default=2000)
+    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
+    args = ap.parse_args()
+    os.makedirs(args.out_dir, exist_ok=True)
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

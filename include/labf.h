@@ -1,0 +1,303 @@
+/*
+ * labf.h -- C ABI of the GB300 multiple-walker lambda-ABF engine.
+ *
+ * The engine advances many walkers of one or more systems with Langevin
+ * lambda-dynamics under an Adaptive Biasing Force on lambda (arXiv
+ * 2307.08006, Sec. 2.1-2.4).  Each walker carries atoms (x, v) and an
+ * extended lambda particle (lambda, p_lambda).  One MD step evaluates the
+ * alchemically scaled soft-core Lennard-Jones + reaction-field pair forces
+ * and, in the same pair pass, the walker's dU/dlambda; it folds every
+ * walker's dU/dlambda into the shared lambda-binned accumulator of its
+ * stage (sum, sum of squares, count); it applies ramp * bin mean as the
+ * bias on lambda; and it advances atoms and lambda with BAOAB.  The
+ * accumulator's running mean integrated over lambda is Delta A (Sec. 2.3).
+ *
+ * The calls mirror the engine <-> Colvars contract of Sec. 3.2: parameters
+ * are fixed once (la_create_system); each step the engine computes forces
+ * and dU/dlambda at the current lambda, the bias is updated from the
+ * accumulator and lambda is advanced (la_step_walkers); the free-energy
+ * estimate is read back on demand (la_read_abf).
+ *
+ * Conventions for every call:
+ *   - All calls are extern "C", return an int status (LA_OK = 0, negative
+ *     LA_ERR_* on failure) and throw no C++ exception across the ABI.
+ *   - "host" pointers are ordinary CPU memory owned by the caller; "device"
+ *     pointers are CUDA global memory owned by the caller.  The library
+ *     never frees caller memory.
+ *   - Device work is enqueued on the caller's stream (cudaStream_t passed as
+ *     void*; NULL = the legacy default stream).  Calls marked
+ *     "synchronising" wait for that stream before returning.
+ *   - After an error, la_last_error(h) gives a message; a device-side error
+ *     (list overflow, non-finite state, fixed-point overflow) is sticky:
+ *     further stepping calls return LA_ERR_STATE until la_destroy.
+ *
+ * Units are the caller's (reduced LJ units, or nm, ps, amu, kJ/mol, e);
+ * the engine only requires them to be consistent.
+ */
+#ifndef LABF_H
+#define LABF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define LA_OK 0
+#define LA_ERR_INVALID_ARG (-1)
+#define LA_ERR_BOX_TOO_SMALL (-2)   /* box edge < 2 (r_cut + skin) */
+#define LA_ERR_CUDA (-3)
+#define LA_ERR_UNSUPPORTED (-4)
+#define LA_ERR_ARENA_TOO_SMALL (-5)
+#define LA_ERR_LIST_OVERFLOW (-6)   /* a neighbour-list capacity was exceeded */
+#define LA_ERR_NONFINITE (-7)       /* NaN/Inf appeared in positions or lambda */
+#define LA_ERR_FIXED_OVERFLOW (-8)  /* a force exceeded the 64-bit fixed-point range */
+#define LA_ERR_STATE (-9)           /* the handle is in a sticky error state */
+
+/* ---- device status bits (la_sync / la_status) ---- */
+#define LA_STATUS_LIST_OVERFLOW 0x1u
+#define LA_STATUS_NONFINITE 0x2u
+#define LA_STATUS_FIXED_OVERFLOW 0x4u
+#define LA_STATUS_COLUMN_OVERFLOW 0x8u
+#define LA_STATUS_ALCH_OVERFLOW 0x10u
+
+/* ---- energy terms reported by la_energy_forces ---- */
+#define LA_N_TERMS 7 /* LJ, RF, soft-core LJ, scaled RF, bond, angle, restraint */
+
+/* ---- flags of la_energy_forces ---- */
+#define LA_EF_REBUILD 0x1u      /* rebuild the neighbour lists first (positions were set) */
+#define LA_EF_COUNT_PAIRS 0x2u  /* count in-cutoff pairs (returned by la_stats) */
+
+typedef struct la_handle la_handle;
+
+/*
+ * One system: topology, force field, alchemical and ABF parameters, and the
+ * initial state of its walkers.  All pointers are host memory, read during
+ * la_query_sizes / la_create_system only (copied).
+ *
+ *   Force field (Sec. 3.1.2): pairs interact with Lennard-Jones
+ *   (Lorentz-Berthelot mixing of per-atom sigma, epsilon) and reaction-field
+ *   electrostatics coul*q_i*q_j*(1/r + k_rf r^2 - c_rf), both truncated at
+ *   r_cut.  A pair with exactly one alchemical atom is scaled: soft-core LJ
+ *   lambda_v^sc_n 4 eps (s^-2 - s^-1), s = sc_alpha (1-lambda_v)^sc_m +
+ *   (r/sigma)^6, and lambda_e times the RF term.  Pairs of two alchemical
+ *   atoms, pairs in the same excl_group (>= 0) and pairs listed in
+ *   excl_extra are excluded.  lambda -> (lambda_v, lambda_e) is the
+ *   piecewise-linear path of Sec. 3.1.1 with breakpoints b_v, b_e.
+ *   eps_rf <= 0 selects a conducting continuum.
+ *
+ *   Dynamics (Sec. 2.1, 2.2, Eq. lambda-abf; SI S1): BAOAB with collision
+ *   rates gamma (atoms) and gamma_lambda (lambda), temperature kT, time step
+ *   dt, lambda mass m_lambda.  lambda is reflected at its stage's walls.
+ *   lambda_dynamics = 0 freezes lambda (fixed-lambda windows).
+ *
+ *   ABF (Sec. 2.3, 3.3, 2.4): n_stages stages, each with its own lambda
+ *   interval [stage_lo, stage_hi], stage_bins bins and stage_walkers
+ *   walkers (walkers are ordered by stage).  The bias is
+ *   min(1, n_k / n_full) * (bin mean); walkers merge their samples into the
+ *   shared statistics every shared_freq steps.  abf_on = 0 disables the bias.
+ *
+ *   Initial state: x0, v0 are [W][n_atoms][3] float32 (W = total walkers of
+ *   the system), lam0 and plam0 are [W] double.  Philox streams are keyed by
+ *   (seed, walker index within the system).
+ */
+typedef struct {
+    int32_t n_atoms;
+    double box; /* cubic box edge L */
+    const double *mass, *charge, *sigma, *epsilon; /* [n_atoms] */
+    const uint8_t *alch;                           /* [n_atoms] 1 = alchemical */
+    const int32_t *excl_group;                     /* [n_atoms], -1 = none */
+    const int32_t *excl_extra;                     /* [n_atoms][4], -1 padded */
+    int32_t n_bonds;  const int32_t *bond_ij;   const double *bond_r0, *bond_k;
+    int32_t n_angles; const int32_t *angle_ijk; const double *angle_t0, *angle_k;
+    int32_t n_posres; const int32_t *posres_idx; const double *posres_x0; double posres_k;
+    int32_t n_fb_a; const int32_t *fb_a; int32_t n_fb_b; const int32_t *fb_b;
+    double fb_d0, fb_k;                            /* flat-bottom on |COM_a - COM_b| */
+    int32_t n_lh; const int32_t *lh_idx; const double *lh_x0;
+    double lh_k0, lh_k1; int32_t lh_dims;          /* 1/2 k(lambda) |x - x0|^2 */
+    double r_cut, eps_rf, coul;
+    double b_v, b_e, sc_alpha; int32_t sc_n, sc_m;
+    double kT, dt, gamma, m_lambda, gamma_lambda, skin, n_full;
+    int32_t shared_freq; uint32_t seed;
+    int32_t lambda_dynamics, abf_on, theta_stats;
+    int32_t n_stages;
+    const double *stage_lo, *stage_hi;
+    const int32_t *stage_bins, *stage_walkers;
+    const float *x0, *v0;       /* [W][n_atoms][3] */
+    const double *lam0, *plam0; /* [W] */
+} la_system_desc;
+
+/* Engine options; zero-initialise for defaults. */
+typedef struct {
+    int32_t graph_steps;         /* MD steps captured per CUDA-graph replay (default 10) */
+    int32_t autotune;            /* 1: pick pair-kernel launch shape by timing at create */
+    double list_capacity_factor; /* >= 1 safety factor on list capacities (default 1.6) */
+    int32_t pair_warps;          /* warps per CTA of the pair kernel (0 = default) */
+    int32_t pair_ctas_per_sm;    /* resident CTAs per SM of the pair kernel (0 = default) */
+    int32_t chunk_entries;       /* cluster-pair entries per warp work item (0 = default) */
+} la_options;
+
+/*
+ * la_query_sizes: bytes of device memory the engine needs for these systems
+ * (one arena, 256-byte aligned).  Host-only; no device work.
+ * Errors: LA_ERR_INVALID_ARG (bad counts, sizes or parameters),
+ * LA_ERR_BOX_TOO_SMALL (L < 2 (r_cut + skin)).
+ */
+int la_query_sizes(const la_system_desc *sys, int n_sys, const la_options *opt,
+                   size_t *arena_bytes);
+
+/*
+ * la_create_system: build an engine for n_sys systems (Sec. 3.2: parameters
+ * initialised once).  `arena` is caller-owned device memory of at least
+ * la_query_sizes bytes, 256-byte aligned; the engine carves all of its
+ * device state out of it and never allocates device memory itself.  The
+ * initial state is uploaded, neighbour lists are built and forces,
+ * dU/dlambda and the lambda force are evaluated (no sample is folded).
+ * Synchronising on `stream`.  On success *out owns host metadata and CUDA
+ * graphs only.  Errors: LA_ERR_INVALID_ARG, LA_ERR_BOX_TOO_SMALL,
+ * LA_ERR_ARENA_TOO_SMALL, LA_ERR_CUDA, LA_ERR_LIST_OVERFLOW.
+ */
+int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt, void *arena,
+                     size_t arena_bytes, void *stream, la_handle **out);
+
+/*
+ * la_step_walkers: advance every walker of every system by n_steps BAOAB
+ * steps with the ABF fold and bias each step (Eq. lambda-abf; Sec. 2.4 with
+ * sharing every shared_freq steps), as one batched launch sequence per step
+ * replayed from a CUDA graph.  Asynchronous: returns after enqueueing on
+ * `stream`; it first checks the status word left by earlier calls and
+ * returns LA_ERR_STATE (with la_last_error) if a device error was recorded.
+ */
+int la_step_walkers(la_handle *h, int64_t n_steps, void *stream);
+
+/*
+ * la_step_walkers_plain: the same n_steps, issued as one launch sequence per
+ * walker and per phase without CUDA graphs (the one-walker-per-launch
+ * form).  Results are identical to la_step_walkers.  Asynchronous.
+ */
+int la_step_walkers_plain(la_handle *h, int64_t n_steps, void *stream);
+
+/*
+ * la_read_abf: the accumulator of stage `stage` of system `sys` and its TI
+ * read-out (Sec. 2.3): per bin k the sum, sum of squares and count of
+ * dU/dlambda samples, grad[k] = sum/count (NaN for an empty bin), the
+ * Riemann sum A[k] at the bin edges (A has n_bins + 1 entries, A[0] = 0),
+ * *dA = A[n_bins], and *dA_se = w * sqrt(sum_k var_k / n_k), a naive
+ * standard error that ignores time correlation.  Samples not yet merged
+ * (shared_freq > 1) are not included.  Any output pointer may be NULL.
+ * Host arrays, caller-owned.  Synchronising.  Returns LA_OK, or 1
+ * (LA_WARN_EMPTY_BIN) when a bin is empty.
+ */
+#define LA_WARN_EMPTY_BIN 1
+int la_read_abf(la_handle *h, int sys, int stage, double *sum, double *sumsq, int64_t *count,
+                double *grad, double *A, double *dA, double *dA_se, void *stream);
+
+/*
+ * la_energy_forces: energies and forces of one walker (global walker index)
+ * at its current state (Sec. 3.2: the engine's gradient routine).
+ * energy_terms (host, may be NULL): [LA_N_TERMS] doubles.
+ * forces (device, may be NULL): [n_atoms][3] float32, -dU/dx.
+ * dUdl (host, may be NULL): dU/dlambda.
+ * dUdtheta, d2Udl_dtheta (host, may be NULL): [P] doubles with
+ * P = 3 n_alch + 1: (eps, sigma, q) of each alchemical atom in index order,
+ * then k1 of the lambda-switched well; dU/dtheta and d2U/dlambda dtheta.
+ * flags: LA_EF_REBUILD to rebuild the lists first (needed after positions
+ * were set by la_set_state), LA_EF_COUNT_PAIRS to count in-cutoff pairs.
+ * The walker's stored force is refreshed as a side effect.  Synchronising.
+ */
+int la_energy_forces(la_handle *h, int walker, uint32_t flags, double *energy_terms,
+                     float *forces, double *dUdl, double *dUdtheta, double *d2Udl_dtheta,
+                     void *stream);
+
+/*
+ * la_get_state / la_set_state: positions, velocities (host [n][3] float32),
+ * lambda and p_lambda (host double) and the step counter of one walker, in
+ * the system's atom order.  la_set_state rebuilds the lists and re-evaluates
+ * forces (no sample is folded).  Any pointer may be NULL (left unchanged /
+ * not read).  Synchronising.
+ */
+int la_get_state(la_handle *h, int walker, float *x, float *v, double *lam, double *plam,
+                 uint64_t *step, void *stream);
+int la_set_state(la_handle *h, int walker, const float *x, const float *v, const double *lam,
+                 const double *plam, void *stream);
+
+/*
+ * la_set_alch_params: replace (epsilon, sigma, charge) of the alchemical
+ * atoms of system `sys` (host [n_alch][3] double, alchemical atoms in index
+ * order) for the differentiation path; forces are re-evaluated.
+ * Synchronising.
+ */
+int la_set_alch_params(la_handle *h, int sys, const double *theta, void *stream);
+
+/*
+ * la_read_theta: per-bin theta statistics of stage `stage` of system `sys`
+ * (theta_stats = 1): sums of d2U/dlambda dtheta, of dU/dtheta and of
+ * dU/dlambda * dU/dtheta, each host [n_bins][P].  Synchronising.
+ */
+int la_read_theta(la_handle *h, int sys, int stage, double *sum_d2, double *sum_d, double *sum_sd,
+                  void *stream);
+
+/*
+ * la_get_pairs: expand the current neighbour list of one walker into atom
+ * pairs (i < j, system atom indices) with kind 0 (normal) or 1 (one atom
+ * alchemical), sorted by (i, j).  `pairs` is host [cap][2] int32, `kind`
+ * host [cap] uint8; *count receives the total (may exceed cap).  Debug /
+ * parity aid.  Synchronising.
+ */
+int la_get_pairs(la_handle *h, int walker, int32_t *pairs, uint8_t *kind, int64_t cap,
+                 int64_t *count, void *stream);
+
+/*
+ * la_lambda_path: lambda -> {lambda_v, lambda_e, dlambda_v/dlambda,
+ * dlambda_e/dlambda} (Sec. 3.1.1) evaluated by the engine's device code for
+ * n values with breakpoints b_v, b_e, staged through the handle's I/O
+ * buffer (n up to a few thousand; LA_ERR_INVALID_ARG beyond).
+ * lam: host [n]; out: host [n][4].  Synchronising.
+ */
+int la_lambda_path(la_handle *h, const double *lam, int n, double b_v, double b_e, double *out,
+                   void *stream);
+
+/*
+ * la_sync: wait for `stream`, then return the status as an LA_ERR_* code
+ * (LA_OK if clean); *status_bits (may be NULL) receives LA_STATUS_* bits.
+ */
+int la_sync(la_handle *h, void *stream, uint32_t *status_bits);
+
+/*
+ * la_stats: counters since creation.  out (host, may be NULL) receives
+ *   [0] MD steps taken, [1] list rebuilds (summed over walkers),
+ *   [2] kernel launches issued by the engine (graph nodes counted per replay),
+ *   [3] in-cutoff normal pairs counted by the last LA_EF_COUNT_PAIRS call,
+ *   [4] in-cutoff alchemical pairs counted by that call,
+ *   [5] cluster-pair entries in the current lists (all walkers),
+ *   [6] reserved (-1).
+ * Synchronising.
+ */
+#define LA_N_STATS 7
+int la_stats(la_handle *h, int64_t *out, void *stream);
+
+/*
+ * la_time_kernels: run n_steps batched steps outside the graph with CUDA
+ * events around each kernel on `stream`; ms_out (host [LA_N_KERNELS])
+ * receives the mean device milliseconds per launch of each kernel class,
+ * launches_out (host [LA_N_KERNELS], may be NULL) the launch counts.
+ * Synchronising.
+ */
+#define LA_N_KERNELS 6 /* integrate, rebuild (all list kernels), pairs, bonded, walker, lambda */
+int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_out, void *stream);
+
+/* la_autotune_report: text describing the chosen launch shapes (static buffer). */
+const char *la_autotune_report(la_handle *h);
+
+/* la_last_error: message of the last failing call on h (static per handle). */
+const char *la_last_error(la_handle *h);
+
+/* la_destroy: free host metadata and CUDA graphs; never touches the arena. */
+int la_destroy(la_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LABF_H */

@@ -1,0 +1,578 @@
+// k_list.cu -- neighbour-list rebuild: integer quantization, spatial sort
+// into super-clusters, cluster-pair list with exact atom-pair masks, and the
+// alchemical pair list.
+//
+// The listed pair set is defined on integer coordinates so that it is
+// bit-exact and independent of floating-point contraction:
+//   u = floor(frac(x L^-1) 2^24) (one rounded FP64 product),
+//   d = ((u_i - u_j + 2^23) mod 2^24) - 2^23 per component,
+//   listed iff D = |d|^2 < R = floor((r_list L^-1)^2 2^48), i < j, the pair is
+//   not excluded, and at most one atom is alchemical.
+// Each unordered pair appears in exactly one cluster-pair entry: the entry
+// whose periodic shift equals the pair's minimum image, with the half-list
+// rule (the j super-cluster less than half-way round the index circle from
+// the i super-cluster, or the same one with a positive shift, or the same
+// one with shift 0 and slot_i < slot_j).
+#include "labf_internal.cuh"
+#include "labf_launch.h"
+
+namespace labf {
+
+// -------------------------------------------------------------------------
+// R1: quantize every real slot and count atoms per xy column
+// -------------------------------------------------------------------------
+__global__ void k_quantize(Dev d, int g0, int g1) {
+    const int nthr = gridDim.x * blockDim.x;
+    for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += nthr) {
+        const int w = d.slot_walker[g];
+        if (!d.rebuild[w]) continue;
+        const int a = d.atom_of_slot[g];
+        if (a < 0) continue;
+        const WalkerDev &W = d.walk[w];
+        const SysDev &S = d.sys[W.sys];
+        const float4 x = d.xq[g];
+        const uint32_t ux = quantize(x.x, S.box_inv), uy = quantize(x.y, S.box_inv),
+                       uz = quantize(x.z, S.box_inv);
+        const int cx = (int)(((unsigned long long)ux * (unsigned)S.ncx) >> 24);
+        const int cy = (int)(((unsigned long long)uy * (unsigned)S.ncx) >> 24);
+        const int c = cx + S.ncx * cy;
+        d.t_uq[g] = make_int4((int)ux, (int)uy, (int)uz, a);
+        d.t_col[g] = c;
+        d.t_pos[g] = atomicAdd(&d.col_count[W.col_off + c], 1);
+    }
+}
+
+// R2: per walker, prefix sums of column counts and super-cluster counts
+__global__ void k_colscan(Dev d, int w0) {
+    const int w = w0 + blockIdx.x;
+    if (!d.rebuild[w]) return;
+    const WalkerDev &W = d.walk[w];
+    if (threadIdx.x == 0) {
+        int acc = 0, sacc = 0;
+        for (int c = 0; c < W.n_cols; ++c) {
+            const int cnt = d.col_count[W.col_off + c];
+            if (cnt > MAX_COL) set_status(d, LA_STATUS_COLUMN_OVERFLOW);
+            const int nsc = (cnt + SC - 1) / SC;
+            d.col_start[W.col_off + c] = acc;
+            d.col_sc[W.col_off + c] = sacc;
+            d.col_nsc[W.col_off + c] = nsc;
+            acc += cnt;
+            sacc += nsc;
+        }
+        if (sacc > W.sc_cap) {
+            set_status(d, LA_STATUS_LIST_OVERFLOW);
+            sacc = W.sc_cap;
+        }
+        d.n_sc[w] = sacc;
+    }
+}
+
+// R3: scatter slot ids into per-column buckets
+__global__ void k_scatter(Dev d, int g0, int g1) {
+    const int nthr = gridDim.x * blockDim.x;
+    for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += nthr) {
+        const int w = d.slot_walker[g];
+        if (!d.rebuild[w] || d.atom_of_slot[g] < 0) continue;
+        const WalkerDev &W = d.walk[w];
+        const int c = d.t_col[g];
+        const int p = d.col_start[W.col_off + c] + d.t_pos[g];
+        d.bucket[W.atom_base + p] = g;
+    }
+}
+
+// R4: sort each column by (u_z, atom id) and cut it into super-clusters of 64
+__global__ void __launch_bounds__(256) k_colsort(Dev d, int w0) {
+    const int w = w0 + blockIdx.y;
+    if (!d.rebuild[w]) return;
+    const WalkerDev &W = d.walk[w];
+    __shared__ unsigned long long key[MAX_COL];
+    __shared__ int slot[MAX_COL];
+    for (int c = blockIdx.x; c < W.n_cols; c += gridDim.x) {
+        const int cnt0 = d.col_count[W.col_off + c];
+        const int cnt = cnt0 > MAX_COL ? MAX_COL : cnt0;
+        const int start = d.col_start[W.col_off + c];
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            const int g = d.bucket[W.atom_base + start + k];
+            const int4 u = d.t_uq[g];
+            key[k] = ((unsigned long long)(unsigned)u.z << 32) | (unsigned)u.w;
+            slot[k] = g;
+        }
+        __syncthreads();
+        const int sc0 = W.sc_off + d.col_sc[W.col_off + c];
+        const int nsc = d.col_nsc[W.col_off + c];
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            const unsigned long long kk = key[k];
+            int r = 0;
+            for (int m = 0; m < cnt; ++m) r += key[m] < kk;
+            const int s = sc0 + r / SC;
+            if (s < W.sc_off + W.sc_cap) d.sc_member[(size_t)s * SC + (r % SC)] = slot[k];
+        }
+        for (int k = threadIdx.x; k < nsc * SC; k += blockDim.x) {
+            const int s = sc0 + k / SC;
+            if (k >= cnt && s < W.sc_off + W.sc_cap) d.sc_member[(size_t)s * SC + (k % SC)] = -1;
+            if ((k % SC) == 0 && s < W.sc_off + W.sc_cap) d.sc_n[s] = min(SC, cnt - (k / SC) * SC);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) d.col_count[W.col_off + c] = 0;  // ready for the next rebuild
+    }
+}
+
+// R5: inside each super-cluster, four k-d splits (longest axis first, ranks
+// by (coordinate, atom id), larger half first) give 16 leaves of <= 4 atoms;
+// leaf k occupies slots 4k..4k+3.  Also the bounding boxes.  One warp per
+// super-cluster.
+__global__ void __launch_bounds__(128) k_kdsplit(Dev d, int w0, int w1) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    __shared__ int sx[4][SC], sy[4][SC], sz[4][SC], sa[4][SC], sg[4][SC], sslot[4][SC];
+    const int nwarp = gridDim.x * (blockDim.x >> 5);
+    const int s_begin = d.walk[w0].sc_off, s_end = d.walk[w1 - 1].sc_off + d.walk[w1 - 1].sc_cap;
+    for (int s = s_begin + blockIdx.x * (blockDim.x >> 5) + wib; s < s_end; s += nwarp) {
+        int lo = w0, hi = w1 - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (d.walk[mid].sc_off <= s) lo = mid; else hi = mid - 1;
+        }
+        const int w = lo;
+        if (!d.rebuild[w]) continue;
+        const WalkerDev &W = d.walk[w];
+        const int s_local = s - W.sc_off;
+        if (s_local >= d.n_sc[w]) continue;
+        const int n = d.sc_n[s];
+        for (int k = lane; k < SC; k += 32) {
+            const int g = k < n ? d.sc_member[(size_t)s * SC + k] : -1;
+            if (g >= 0) {
+                const int4 u = d.t_uq[g];
+                sx[wib][k] = u.x; sy[wib][k] = u.y; sz[wib][k] = u.z; sa[wib][k] = u.w;
+            } else {
+                sa[wib][k] = -1;
+            }
+            sslot[wib][k] = g;
+            sg[wib][k] = 0;
+        }
+        __syncwarp();
+        // leaf index by four binary splits
+        for (int level = 0; level < 4; ++level) {
+            int newg[2];
+            for (int h = 0; h < 2; ++h) {
+                const int k = lane + 32 * h;
+                newg[h] = sg[wib][k];
+                if (k >= n) continue;
+                const int gid = sg[wib][k];
+                int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-1, -1, -1}, cnt = 0;
+                for (int m = 0; m < n; ++m) {
+                    if (sg[wib][m] != gid) continue;
+                    ++cnt;
+                    mn[0] = min(mn[0], sx[wib][m]); mx[0] = max(mx[0], sx[wib][m]);
+                    mn[1] = min(mn[1], sy[wib][m]); mx[1] = max(mx[1], sy[wib][m]);
+                    mn[2] = min(mn[2], sz[wib][m]); mx[2] = max(mx[2], sz[wib][m]);
+                }
+                int ax = 0;
+                if (mx[1] - mn[1] > mx[ax] - mn[ax]) ax = 1;
+                if (mx[2] - mn[2] > mx[ax] - mn[ax]) ax = 2;
+                const int *co = ax == 0 ? sx[wib] : (ax == 1 ? sy[wib] : sz[wib]);
+                const long long mykey = ((long long)co[k] << 32) | (unsigned)sa[wib][k];
+                int r = 0;
+                for (int m = 0; m < n; ++m) {
+                    if (sg[wib][m] != gid) continue;
+                    const long long km = ((long long)co[m] << 32) | (unsigned)sa[wib][m];
+                    r += km < mykey;
+                }
+                newg[h] = 2 * gid + (r >= (cnt + 1) / 2 ? 1 : 0);
+            }
+            __syncwarp();
+            sg[wib][lane] = newg[0];
+            sg[wib][lane + 32] = newg[1];
+            __syncwarp();
+        }
+        // final position inside the leaf: rank by atom id
+        int pos[2];
+        for (int h = 0; h < 2; ++h) {
+            const int k = lane + 32 * h;
+            pos[h] = -1;
+            if (k >= n) continue;
+            int r = 0;
+            for (int m = 0; m < n; ++m) r += (sg[wib][m] == sg[wib][k]) && (sa[wib][m] < sa[wib][k]);
+            pos[h] = sg[wib][k] * JC + r;
+        }
+        // new layout: t_old[new slot] = old slot (-1 for padding)
+        const int gbase = W.slot_off + s_local * SC;
+        d.t_old[gbase + lane] = -1;
+        d.t_old[gbase + lane + 32] = -1;
+        __syncwarp();
+        for (int h = 0; h < 2; ++h)
+            if (pos[h] >= 0) d.t_old[gbase + pos[h]] = sslot[wib][lane + 32 * h];
+        __syncwarp();
+        // bounding boxes (integer, real atoms only): j-clusters, i-clusters, super-cluster
+        if (lane < NJC + NIC + 1) {
+            int first, last;
+            if (lane < NJC) { first = lane; last = lane; }
+            else if (lane < NJC + NIC) { first = 2 * (lane - NJC); last = first + 1; }
+            else { first = 0; last = NJC - 1; }
+            int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-(1 << 30), -(1 << 30), -(1 << 30)}, cnt = 0;
+            for (int m = 0; m < n; ++m) {
+                const int leaf = sg[wib][m];
+                if (leaf < first || leaf > last) continue;
+                ++cnt;
+                mn[0] = min(mn[0], sx[wib][m]); mx[0] = max(mx[0], sx[wib][m]);
+                mn[1] = min(mn[1], sy[wib][m]); mx[1] = max(mx[1], sy[wib][m]);
+                mn[2] = min(mn[2], sz[wib][m]); mx[2] = max(mx[2], sz[wib][m]);
+            }
+            int4 *dst;
+            if (lane < NJC) dst = d.bb_jc + 2 * ((size_t)s * NJC + lane);
+            else if (lane < NJC + NIC) dst = d.bb_ic + 2 * ((size_t)s * NIC + (lane - NJC));
+            else dst = d.bb_sc + 2 * (size_t)s;
+            dst[0] = make_int4(mn[0], mn[1], mn[2], cnt);
+            dst[1] = make_int4(mx[0], mx[1], mx[2], 0);
+        }
+        __syncwarp();
+    }
+}
+
+// R6: gather the state into the new slot order (scratch buffers)
+__global__ void k_permute_gather(Dev d, int g0, int g1) {
+    const int nthr = gridDim.x * blockDim.x;
+    for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += nthr) {
+        const int w = d.slot_walker[g];
+        if (!d.rebuild[w]) continue;
+        const WalkerDev &W = d.walk[w];
+        const int local = g - W.slot_off;
+        const int s_local = local / SC;
+        int old = -1;
+        if (s_local < d.n_sc[w]) old = d.t_old[g];
+        if (old >= 0) {
+            d.t_xq[g] = d.xq[old];
+            d.t_vv[g] = d.vv[old];
+            d.uq[g] = d.t_uq[old];
+        } else {
+            // padding: park on a real atom of the same super-cluster (finite,
+            // never listed) or, for unused super-clusters, at the origin
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (s_local < d.n_sc[w]) {
+                const int first = d.sc_member[(size_t)(W.sc_off + s_local) * SC];
+                if (first >= 0) p = d.xq[first];
+            }
+            p.w = 0.f;
+            d.t_xq[g] = p;
+            d.t_vv[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+            d.uq[g] = make_int4(0, 0, 0, -1);
+        }
+    }
+}
+
+// R7: write the new layout back and refresh per-slot parameters
+__global__ void k_permute_scatter(Dev d, int g0, int g1) {
+    const int nthr = gridDim.x * blockDim.x;
+    for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += nthr) {
+        const int w = d.slot_walker[g];
+        if (!d.rebuild[w]) continue;
+        const WalkerDev &W = d.walk[w];
+        const SysDev &S = d.sys[W.sys];
+        const int a = d.uq[g].w;
+        float4 x = d.t_xq[g];
+        // wrap into [0, L) (the list built from this layout assumes it)
+        x.x -= S.boxf * floorf(x.x * S.box_invf);
+        x.y -= S.boxf * floorf(x.y * S.box_invf);
+        x.z -= S.boxf * floorf(x.z * S.box_invf);
+        d.vv[g] = d.t_vv[g];
+        d.atom_of_slot[g] = a;
+        if (a >= 0) {
+            const float4 ap = d.aparam_mut[S.atom_off + a];
+            x.w = ap.x;
+            d.lj[g] = make_float2(ap.y, ap.z);
+            d.im[g] = make_float2(ap.w, d.anoise[S.atom_off + a]);
+            d.slot_of_atom[W.atom_base + a] = g;
+        } else {
+            d.lj[g] = make_float2(0.f, 0.f);
+            d.im[g] = make_float2(0.f, 0.f);
+        }
+        d.xq[g] = x;
+        d.xref[g] = x;
+    }
+}
+
+// -------------------------------------------------------------------------
+// R8: cluster-pair list.  One warp per super-cluster S; lane = ia + 8 jb
+// tests the pair (i-slot 8 ic + ia, j-slot 4 jc + jb) exactly.
+// -------------------------------------------------------------------------
+__device__ __forceinline__ long long bb_dist2(const int4 &alo, const int4 &ahi, const int4 &blo,
+                                              const int4 &bhi, int sx, int sy, int sz) {
+    long long dx = max(0, max(blo.x + sx - ahi.x, alo.x - (bhi.x + sx)));
+    long long dy = max(0, max(blo.y + sy - ahi.y, alo.y - (bhi.y + sy)));
+    long long dz = max(0, max(blo.z + sz - ahi.z, alo.z - (bhi.z + sz)));
+    return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+__device__ __forceinline__ bool excluded(const Dev &d, const SysDev &S, int a, int b) {
+    const int ga = d.agroup[S.atom_off + a];
+    if (ga >= 0 && ga == d.agroup[S.atom_off + b]) return true;
+    const int4 ea = d.aexcl[S.atom_off + a];
+    if (ea.x == b || ea.y == b || ea.z == b || ea.w == b) return true;
+    const int4 eb = d.aexcl[S.atom_off + b];
+    return eb.x == a || eb.y == a || eb.z == a || eb.w == a;
+}
+
+__global__ void __launch_bounds__(128) k_listbuild(Dev d, int w0, int w1) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int ia = lane & 7, jb = lane >> 3;
+    __shared__ int4 s_u[4][SC];
+    __shared__ int4 s_bb[4][2 * NIC + 2];
+    const int nwarp = gridDim.x * (blockDim.x >> 5);
+    const int s_begin = d.walk[w0].sc_off, s_end = d.walk[w1 - 1].sc_off + d.walk[w1 - 1].sc_cap;
+    for (int s = s_begin + blockIdx.x * (blockDim.x >> 5) + wib; s < s_end; s += nwarp) {
+        int lo = w0, hi = w1 - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (d.walk[mid].sc_off <= s) lo = mid; else hi = mid - 1;
+        }
+        const int w = lo;
+        if (!d.rebuild[w]) continue;
+        const WalkerDev &W = d.walk[w];
+        const SysDev &S = d.sys[W.sys];
+        const int S_loc = s - W.sc_off;
+        const int nsc = d.n_sc[w];
+        if (S_loc >= nsc) {
+            if (lane == 0) d.sc_nent[s] = 0;
+            continue;
+        }
+        const int gS = W.slot_off + S_loc * SC;
+        s_u[wib][lane] = d.uq[gS + lane];
+        s_u[wib][lane + 32] = d.uq[gS + lane + 32];
+        if (lane < 2 * NIC) s_bb[wib][lane] = d.bb_ic[2 * (size_t)s * NIC + lane];
+        if (lane < 2) s_bb[wib][2 * NIC + lane] = d.bb_sc[2 * (size_t)s + lane];
+        __syncwarp();
+        const int4 slo = s_bb[wib][2 * NIC], shi = s_bb[wib][2 * NIC + 1];
+        const long long R = S.R;
+        const int U = 1 << 24;
+        const int ncx = S.ncx;
+        const int cx0 = (int)(((long long)(slo.x - S.Rq) * ncx) >> 24);
+        const int cx1 = (int)(((long long)(shi.x + S.Rq) * ncx) >> 24);
+        const int cy0 = (int)(((long long)(slo.y - S.Rq) * ncx) >> 24);
+        const int cy1 = (int)(((long long)(shi.y + S.Rq) * ncx) >> 24);
+        int nent = 0;
+        const size_t ebase = (size_t)s * d.ent_cap;
+        for (int cy = cy0; cy <= cy1; ++cy) {
+            const int ty = floordiv(cy, ncx), wy = cy - ty * ncx;
+            for (int cx = cx0; cx <= cx1; ++cx) {
+                const int tx = floordiv(cx, ncx), wx = cx - tx * ncx;
+                const int col = wx + ncx * wy;
+                const int t0 = d.col_sc[W.col_off + col], tn = d.col_nsc[W.col_off + col];
+                for (int T_loc = t0; T_loc < t0 + tn && T_loc < nsc; ++T_loc) {
+                    // cyclic half list over super-clusters: T is S's partner
+                    // when it lies less than half-way round the index circle
+                    if (T_loc != S_loc) {
+                        const int del = T_loc > S_loc ? T_loc - S_loc : T_loc - S_loc + nsc;
+                        if (2 * del > nsc || (2 * del == nsc && T_loc < S_loc)) continue;
+                    }
+                    const int t = W.sc_off + T_loc;
+                    const int4 tlo = d.bb_sc[2 * (size_t)t], thi = d.bb_sc[2 * (size_t)t + 1];
+                    if (tlo.w == 0) continue;
+                    for (int tz = -1; tz <= 1; ++tz) {
+                        if (T_loc == S_loc) {  // self: only shift 0 or lexicographically positive
+                            if (tx < 0 || (tx == 0 && (ty < 0 || (ty == 0 && tz < 0)))) continue;
+                        }
+                        const int shx = tx * U, shy = ty * U, shz = tz * U;
+                        if (bb_dist2(slo, shi, tlo, thi, shx, shy, shz) >= R) continue;
+                        const bool self0 = (T_loc == S_loc) && tx == 0 && ty == 0 && tz == 0;
+                        const int shift_code = (tx + 1) + 3 * (ty + 1) + 9 * (tz + 1);
+                        for (int jc = 0; jc < NJC; ++jc) {
+                            const int4 jlo = d.bb_jc[2 * ((size_t)t * NJC + jc)];
+                            if (jlo.w == 0) continue;
+                            const int4 jhi = d.bb_jc[2 * ((size_t)t * NJC + jc) + 1];
+                            if (bb_dist2(slo, shi, jlo, jhi, shx, shy, shz) >= R) continue;
+                            const int gj = W.slot_off + T_loc * SC + jc * JC + jb;
+                            const int4 uj = d.uq[gj];
+                            const bool jreal = uj.w >= 0 && !d.aalch[S.atom_off + max(uj.w, 0)];
+                            unsigned masks[NIC];
+                            unsigned imask = 0;
+#pragma unroll
+                            for (int ic = 0; ic < NIC; ++ic) {
+                                masks[ic] = 0;
+                                const int4 ilo = s_bb[wib][2 * ic], ihi = s_bb[wib][2 * ic + 1];
+                                if (ilo.w == 0) continue;
+                                if (bb_dist2(ilo, ihi, jlo, jhi, shx, shy, shz) >= R) continue;
+                                const int4 ui = s_u[wib][ic * IC + ia];
+                                bool ok = jreal && ui.w >= 0;
+                                if (ok) ok = !d.aalch[S.atom_off + ui.w];
+                                if (ok && self0) ok = (ic * IC + ia) < (jc * JC + jb);
+                                if (ok) {
+                                    const int dx = uj.x + shx - ui.x, dy = uj.y + shy - ui.y, dz = uj.z + shz - ui.z;
+                                    const int H = 1 << 23;
+                                    ok = dx >= -H && dx < H && dy >= -H && dy < H && dz >= -H && dz < H;
+                                    if (ok) {
+                                        const long long D = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+                                        ok = D < R;
+                                    }
+                                }
+                                if (ok) ok = !excluded(d, S, ui.w, uj.w);
+                                masks[ic] = __ballot_sync(0xffffffffu, ok);
+                                if (masks[ic]) imask |= 1u << ic;
+                            }
+                            if (imask) {
+                                if (nent < d.ent_cap) {
+                                    const size_t e = ebase + nent;
+                                    if (lane == 0)
+                                        d.ent_hdr[e] = make_int2(W.slot_off + T_loc * SC + jc * JC,
+                                                                 shift_code | (int)(imask << 8));
+                                    if (lane == 1)
+                                        d.ent_mask[2 * e] = make_uint4(masks[0], masks[1], masks[2], masks[3]);
+                                    if (lane == 2)
+                                        d.ent_mask[2 * e + 1] = make_uint4(masks[4], masks[5], masks[6], masks[7]);
+                                } else if (lane == 0) {
+                                    set_status(d, LA_STATUS_LIST_OVERFLOW);
+                                }
+                                ++nent;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (lane == 0) d.sc_nent[s] = min(nent, d.ent_cap);
+        __syncwarp();
+    }
+}
+
+// -------------------------------------------------------------------------
+// R9: alchemical list: one warp per (walker, alchemical atom) scans the
+// walker's slots in order (deterministic output order)
+// -------------------------------------------------------------------------
+__global__ void k_alchlist(Dev d, int w0, int w1, int a0, int a1) {
+    const int lane = threadIdx.x & 31;
+    const int nwarp = gridDim.x * (blockDim.x >> 5);
+    for (int it = a0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < a1; it += nwarp) {
+        int lo = w0, hi = w1 - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (d.walk[mid].alch_base <= it) lo = mid; else hi = mid - 1;
+        }
+        const int w = lo;
+        if (!d.rebuild[w]) continue;
+        const WalkerDev &W = d.walk[w];
+        const SysDev &S = d.sys[W.sys];
+        const int r = it - W.alch_base;
+        const int a = d.alch_atoms[S.alch_off + r];
+        const int4 ua = d.uq[d.slot_of_atom[W.atom_base + a]];
+        int cnt = 0;
+        const int nslots = d.n_sc[w] * SC;
+        int *out = d.alch_slot + (size_t)it * d.alch_cap;
+        for (int k0 = 0; k0 < nslots; k0 += 32) {
+            const int g = W.slot_off + k0 + lane;
+            bool ok = false;
+            if (k0 + lane < nslots) {
+                const int4 ub = d.uq[g];
+                if (ub.w >= 0 && !d.aalch[S.atom_off + ub.w]) {
+                    const long long dx = torus_delta(ub.x, ua.x), dy = torus_delta(ub.y, ua.y),
+                                    dz = torus_delta(ub.z, ua.z);
+                    ok = dx * dx + dy * dy + dz * dz < S.R && !excluded(d, S, a, ub.w);
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+            if (ok && pos < d.alch_cap) out[pos] = g;
+            cnt += __popc(m);
+        }
+        if (cnt > d.alch_cap) {
+            if (lane == 0) set_status(d, LA_STATUS_ALCH_OVERFLOW);
+            cnt = d.alch_cap;
+        }
+        if (lane == 0) d.alch_cnt[it] = cnt;
+    }
+}
+
+// -------------------------------------------------------------------------
+// R10: pair-kernel work items (chunks of `chunk` entries of one
+// super-cluster), per walker; clears the rebuild flag.
+// -------------------------------------------------------------------------
+__global__ void k_items(Dev d, int w0) {
+    const int w = w0 + blockIdx.x;
+    if (!d.rebuild[w]) return;
+    const WalkerDev &W = d.walk[w];
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int nsc = d.n_sc[w];
+    for (int base = 0; base < nsc; base += blockDim.x) {
+        const int sl = base + threadIdx.x;
+        const int ne = sl < nsc ? d.sc_nent[W.sc_off + sl] : 0;
+        const int nch = (ne + d.chunk - 1) / d.chunk;
+        // block exclusive scan of nch
+        int v = nch;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) wsum[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            int t = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int u = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += u;
+            }
+            wsum[lane] = t;
+        }
+        __syncthreads();
+        const int excl = carry + v - nch + (wid > 0 ? wsum[wid - 1] : 0);
+        for (int c = 0; c < nch; ++c) {
+            const int item = excl + c;
+            if (item < W.item_cap) {
+                const int e0 = c * d.chunk, e1 = min(ne, e0 + d.chunk);
+                d.items[W.item_base + item] = make_int4(W.sc_off + sl, e0, e1, w);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + nch;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (carry > W.item_cap) set_status(d, LA_STATUS_LIST_OVERFLOW);
+        d.n_items[w] = min(carry, W.item_cap);
+        d.rebuild[w] = 0;
+        atomicAdd(&d.counters[0], 1ull);
+    }
+}
+
+// -------------------------------------------------------------------------
+// host launcher of the whole rebuild chain (every kernel exits early for
+// walkers whose rebuild flag is clear)
+// -------------------------------------------------------------------------
+void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s) {
+    const int g0 = hv.slot_off[w0], g1 = hv.slot_off[w1 - 1] + hv.slot_cap[w1 - 1];
+    int sb = (g1 - g0 + 255) / 256;
+    sb = sb < 1 ? 1 : (sb > hv.n_sm * 8 ? hv.n_sm * 8 : sb);
+    const int nw = w1 - w0;
+    int max_cols = 1;
+    for (int w = w0; w < w1; ++w) max_cols = hv.n_cols[w] > max_cols ? hv.n_cols[w] : max_cols;
+    int nsc = 0;
+    for (int w = w0; w < w1; ++w) nsc += hv.sc_cap[w];
+    int kb = (nsc + 3) / 4;
+    kb = kb < 1 ? 1 : (kb > hv.n_sm * 16 ? hv.n_sm * 16 : kb);
+    const int a0 = hv.alch_base[w0], a1 = hv.alch_base[w1 - 1] + hv.n_alch[w1 - 1];
+    k_quantize<<<sb, 256, 0, s>>>(d, g0, g1);
+    k_colscan<<<nw, 32, 0, s>>>(d, w0);
+    k_scatter<<<sb, 256, 0, s>>>(d, g0, g1);
+    dim3 cg(max_cols < 1024 ? max_cols : 1024, nw);
+    k_colsort<<<cg, 256, 0, s>>>(d, w0);
+    k_kdsplit<<<kb, 128, 0, s>>>(d, w0, w1);
+    k_permute_gather<<<sb, 256, 0, s>>>(d, g0, g1);
+    k_permute_scatter<<<sb, 256, 0, s>>>(d, g0, g1);
+    k_listbuild<<<kb, 128, 0, s>>>(d, w0, w1);
+    if (a1 > a0) {
+        int ab = (a1 - a0 + 3) / 4;
+        ab = ab > hv.n_sm * 8 ? hv.n_sm * 8 : ab;
+        k_alchlist<<<ab, 128, 0, s>>>(d, w0, w1, a0, a1);
+    }
+    k_items<<<nw, 256, 0, s>>>(d, w0);
+}
+
+int rebuild_kernel_count(const HostView &hv, int w0, int w1) {
+    const int a0 = hv.alch_base[w0], a1 = hv.alch_base[w1 - 1] + hv.n_alch[w1 - 1];
+    return a1 > a0 ? 10 : 9;
+}
+
+}  // namespace labf

@@ -1,0 +1,1213 @@
+// labf_api.cu -- host engine behind the C ABI of include/labf.h: layout of
+// the device arena, upload of systems, the batched step as a CUDA graph, the
+// one-walker-per-launch form, read-outs and the launch-shape autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "labf_internal.cuh"
+#include "labf_launch.h"
+
+using namespace labf;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+constexpr int IO_FLOATS_MIN = 1 << 16;
+
+struct SysLayout {
+    int n, n_alch, ncx, n_cols, sc_cap, slot_cap, W, P;
+    double rho, r_list;
+};
+
+struct Layout {
+    std::vector<SysLayout> sys;
+    int W = 0, n_stages = 0, total_bins = 0, max_bins = 0, P_max = 1;
+    long long slots = 0, scs = 0, cols = 0, atoms_w = 0, alch_w = 0, items = 0, bo = 0;
+    long long atoms_s = 0, alch_s = 0, bonds = 0, angles = 0, posres = 0, fb = 0, lh = 0;
+    int ent_cap = 0, alch_cap = 0, chunk = 32, max_n = 0;
+    size_t bytes = 0;
+};
+
+struct Arena {
+    char *base;
+    size_t off, cap;
+    bool dry;
+    template <class T>
+    T *take(size_t count) {
+        off = (off + ALIGN - 1) / ALIGN * ALIGN;
+        T *p = dry ? nullptr : reinterpret_cast<T *>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+double steiner_box(double a, double b, double c, double r) {
+    // volume of the box a x b x c dilated by a ball of radius r
+    const double pi = 3.14159265358979323846;
+    return a * b * c + 2.0 * (a * b + b * c + c * a) * r + pi * (a + b + c) * r * r +
+           4.0 / 3.0 * pi * r * r * r;
+}
+
+int validate(const la_system_desc *sys, int n_sys, std::string &err) {
+    if (!sys || n_sys <= 0) { err = "no systems"; return LA_ERR_INVALID_ARG; }
+    int W = 0;
+    for (int s = 0; s < n_sys; ++s) {
+        const la_system_desc &S = sys[s];
+        char buf[256];
+        if (S.n_atoms <= 0 || !S.mass || !S.charge || !S.sigma || !S.epsilon || !S.alch ||
+            !S.excl_group || !S.excl_extra || !S.x0 || !S.v0 || !S.lam0 || !S.plam0) {
+            snprintf(buf, sizeof buf, "system %d: missing atom arrays or initial state", s);
+            err = buf;
+            return LA_ERR_INVALID_ARG;
+        }
+        if (!(S.box > 0) || !(S.r_cut > 0) || !(S.skin >= 0) || !(S.dt > 0) || !(S.kT > 0) ||
+            !(S.m_lambda > 0) || S.n_stages <= 0 || S.n_stages > 16 || !S.stage_lo || !S.stage_hi ||
+            !S.stage_bins || !S.stage_walkers || !(S.b_v > 0) || !(S.b_e < 1) || S.sc_n < 0 ||
+            S.sc_m < 0 || !(S.n_full > 0)) {
+            snprintf(buf, sizeof buf, "system %d: invalid parameters", s);
+            err = buf;
+            return LA_ERR_INVALID_ARG;
+        }
+        if (S.box < 2.0 * (S.r_cut + S.skin)) {
+            snprintf(buf, sizeof buf, "system %d: box %.4g < 2 (r_cut + skin) = %.4g", s, S.box,
+                     2.0 * (S.r_cut + S.skin));
+            err = buf;
+            return LA_ERR_BOX_TOO_SMALL;
+        }
+        for (int k = 0; k < S.n_stages; ++k) {
+            if (S.stage_bins[k] <= 0 || S.stage_walkers[k] < 0 || !(S.stage_hi[k] > S.stage_lo[k]) ||
+                S.stage_lo[k] < 0.0 || S.stage_hi[k] > 1.0) {
+                snprintf(buf, sizeof buf, "system %d: invalid stage %d", s, k);
+                err = buf;
+                return LA_ERR_INVALID_ARG;
+            }
+            W += S.stage_walkers[k];
+        }
+        for (int i = 0; i < S.n_atoms; ++i)
+            if (!(S.mass[i] > 0)) {
+                snprintf(buf, sizeof buf, "system %d: atom %d has non-positive mass", s, i);
+                err = buf;
+                return LA_ERR_INVALID_ARG;
+            }
+        auto chk = [&](int cnt, const int32_t *idx, int per) {
+            if (cnt < 0) return false;
+            if (cnt > 0 && !idx) return false;
+            for (long long k = 0; k < (long long)cnt * per; ++k)
+                if (idx[k] < 0 || idx[k] >= S.n_atoms) return false;
+            return true;
+        };
+        if (!chk(S.n_bonds, S.bond_ij, 2) || !chk(S.n_angles, S.angle_ijk, 3) ||
+            !chk(S.n_posres, S.posres_idx, 1) || !chk(S.n_fb_a, S.fb_a, 1) || !chk(S.n_fb_b, S.fb_b, 1) ||
+            !chk(S.n_lh, S.lh_idx, 1)) {
+            snprintf(buf, sizeof buf, "system %d: topology index out of range", s);
+            err = buf;
+            return LA_ERR_INVALID_ARG;
+        }
+        if ((S.n_bonds && (!S.bond_r0 || !S.bond_k)) || (S.n_angles && (!S.angle_t0 || !S.angle_k)) ||
+            (S.n_posres && !S.posres_x0) || (S.n_lh && !S.lh_x0)) {
+            snprintf(buf, sizeof buf, "system %d: missing topology parameters", s);
+            err = buf;
+            return LA_ERR_INVALID_ARG;
+        }
+    }
+    if (W <= 0 || W > LA_MAX_WALKERS_PER_LAUNCH) {
+        err = "total walkers must be in [1, 256]";
+        return LA_ERR_INVALID_ARG;
+    }
+    return LA_OK;
+}
+
+void compute_layout(const la_system_desc *sys, int n_sys, const la_options *opt, Layout &L) {
+    const double fac = (opt && opt->list_capacity_factor >= 1.0) ? opt->list_capacity_factor : 1.6;
+    L.chunk = (opt && opt->chunk_entries > 0) ? opt->chunk_entries : 32;
+    const double pi = 3.14159265358979323846;
+    double ent_est = 0.0, alch_est = 0.0;
+    for (int s = 0; s < n_sys; ++s) {
+        const la_system_desc &S = sys[s];
+        SysLayout sl{};
+        sl.n = S.n_atoms;
+        sl.n_alch = 0;
+        for (int i = 0; i < S.n_atoms; ++i) sl.n_alch += S.alch[i] ? 1 : 0;
+        sl.P = 3 * sl.n_alch + 1;
+        sl.rho = S.n_atoms / (S.box * S.box * S.box);
+        sl.r_list = S.r_cut + S.skin;
+        const double w_target = std::cbrt(64.0 / sl.rho);
+        sl.ncx = std::max(1, std::min(255, (int)std::floor(S.box / w_target)));
+        sl.n_cols = sl.ncx * sl.ncx;
+        sl.sc_cap = (sl.n + SC - 1) / SC + sl.n_cols;
+        sl.slot_cap = sl.sc_cap * SC;
+        sl.W = 0;
+        for (int k = 0; k < S.n_stages; ++k) sl.W += S.stage_walkers[k];
+        const double wc = S.box / sl.ncx;
+        const double h = std::min(S.box, 64.0 / (sl.rho * wc * wc));
+        const double ej = std::cbrt(4.0 / sl.rho);
+        const double V = steiner_box(wc + ej, wc + ej, h + ej, sl.r_list);
+        const double full = std::min(sl.rho * V / JC, 27.0 * sl.sc_cap * NJC);
+        ent_est = std::max(ent_est, full);
+        alch_est = std::max(alch_est, sl.rho * 4.0 / 3.0 * pi * std::pow(sl.r_list, 3));
+        L.sys.push_back(sl);
+        L.W += sl.W;
+        L.n_stages += S.n_stages;
+        for (int k = 0; k < S.n_stages; ++k) {
+            L.total_bins += S.stage_bins[k];
+            L.max_bins = std::max(L.max_bins, S.stage_bins[k]);
+        }
+        L.P_max = std::max(L.P_max, sl.P);
+        L.max_n = std::max(L.max_n, sl.n);
+        L.slots += (long long)sl.W * sl.slot_cap;
+        L.scs += (long long)sl.W * sl.sc_cap;
+        L.cols += (long long)sl.W * sl.n_cols;
+        L.atoms_w += (long long)sl.W * sl.n;
+        L.alch_w += (long long)sl.W * sl.n_alch;
+        L.bo += (long long)sl.W * (S.n_bonds + S.n_angles + S.n_posres);
+        L.atoms_s += sl.n;
+        L.alch_s += sl.n_alch;
+        L.bonds += S.n_bonds;
+        L.angles += S.n_angles;
+        L.posres += S.n_posres;
+        L.fb += S.n_fb_a + S.n_fb_b;
+        L.lh += S.n_lh;
+    }
+    // the cyclic half list gives each super-cluster about half its neighbourhood
+    L.ent_cap = (int)std::ceil(fac * 0.6 * ent_est) + 64;
+    L.alch_cap = ((int)std::ceil(fac * alch_est) + 64 + 31) / 32 * 32;
+    const int chunks = (L.ent_cap + L.chunk - 1) / L.chunk;
+    L.items = L.scs * chunks;
+}
+
+// carve every device array out of the arena (dry run when base == nullptr)
+size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io_floats,
+             SysDev **sysd, WalkerDev **walkd, StageDev **staged) {
+    Arena a{base, 0, cap, base == nullptr};
+    *sysd = a.take<SysDev>(L.sys.size());
+    *walkd = a.take<WalkerDev>(L.W);
+    *staged = a.take<StageDev>(L.n_stages);
+    d.ap = a.take<float4>(L.atoms_s);
+    d.aparam_mut = a.take<float4>(L.atoms_s);
+    d.anoise = a.take<float>(L.atoms_s);
+    d.agroup = a.take<int>(L.atoms_s);
+    d.aexcl = a.take<int4>(L.atoms_s);
+    d.aalch = a.take<unsigned char>(L.atoms_s);
+    d.alch_atoms = a.take<int>(std::max<long long>(1, L.alch_s));
+    d.bond_ij = a.take<int2>(std::max<long long>(1, L.bonds));
+    d.bond_p = a.take<float2>(std::max<long long>(1, L.bonds));
+    d.angle_ijk = a.take<int4>(std::max<long long>(1, L.angles));
+    d.angle_p = a.take<float2>(std::max<long long>(1, L.angles));
+    d.posres_idx = a.take<int>(std::max<long long>(1, L.posres));
+    d.posres_x0 = a.take<float4>(std::max<long long>(1, L.posres));
+    d.fb_idx = a.take<int>(std::max<long long>(1, L.fb));
+    d.lh_idx = a.take<int>(std::max<long long>(1, L.lh));
+    d.lh_x0 = a.take<float4>(std::max<long long>(1, L.lh));
+    d.xq = a.take<float4>(L.slots);
+    d.vv = a.take<float4>(L.slots);
+    d.xref = a.take<float4>(L.slots);
+    d.lj = a.take<float2>(L.slots);
+    d.im = a.take<float2>(L.slots);
+    d.atom_of_slot = a.take<int>(L.slots);
+    d.slot_walker = a.take<int>(L.slots);
+    d.F = a.take<unsigned long long>(3 * L.slots);
+    d.uq = a.take<int4>(L.slots);
+    d.t_xq = a.take<float4>(L.slots);
+    d.t_vv = a.take<float4>(L.slots);
+    d.t_old = a.take<int>(L.slots);
+    d.t_uq = a.take<int4>(L.slots);
+    d.t_col = a.take<int>(L.slots);
+    d.t_pos = a.take<int>(L.slots);
+    d.bucket = a.take<int>(L.atoms_w);
+    d.slot_of_atom = a.take<int>(L.atoms_w);
+    d.col_count = a.take<int>(L.cols);
+    d.col_start = a.take<int>(L.cols);
+    d.col_sc = a.take<int>(L.cols);
+    d.col_nsc = a.take<int>(L.cols);
+    d.n_sc = a.take<int>(L.W);
+    d.sc_member = a.take<int>(L.scs * SC);
+    d.sc_n = a.take<int>(L.scs);
+    d.bb_sc = a.take<int4>(2 * L.scs);
+    d.bb_ic = a.take<int4>(2 * L.scs * NIC);
+    d.bb_jc = a.take<int4>(2 * L.scs * NJC);
+    d.sc_nent = a.take<int>(L.scs);
+    d.ent_hdr = a.take<int2>(L.scs * (long long)L.ent_cap);
+    d.ent_mask = a.take<uint4>(2 * L.scs * (long long)L.ent_cap);
+    d.items = a.take<int4>(L.items);
+    d.n_items = a.take<int>(L.W);
+    d.alch_cnt = a.take<int>(std::max<long long>(1, L.alch_w));
+    d.alch_slot = a.take<int>(std::max<long long>(1, L.alch_w) * L.alch_cap);
+    d.alch_out = a.take<double>(4 * std::max<long long>(1, L.alch_w));
+    d.alch_th = a.take<double>(6 * std::max<long long>(1, L.alch_w));
+    d.lam = a.take<double>(L.W);
+    d.plam = a.take<double>(L.W);
+    d.G = a.take<double>(L.W);
+    d.s = a.take<double>(L.W);
+    d.dl_direct = a.take<double>(L.W);
+    d.wth = a.take<double>((size_t)L.W * 2 * L.P_max);
+    d.step = a.take<unsigned long long>(L.W);
+    d.pending = a.take<int>(L.W);
+    d.rebuild = a.take<int>(L.W);
+    d.eterm = a.take<long long>((size_t)L.W * N_ETERMS);
+    d.abf_sum = a.take<double>(L.total_bins);
+    d.abf_sumsq = a.take<double>(L.total_bins);
+    d.abf_count = a.take<unsigned long long>(L.total_bins);
+    d.dl_sum = a.take<double>((size_t)L.W * L.max_bins);
+    d.dl_sumsq = a.take<double>((size_t)L.W * L.max_bins);
+    d.dl_count = a.take<unsigned long long>((size_t)L.W * L.max_bins);
+    d.th_d2 = a.take<double>((size_t)L.total_bins * L.P_max);
+    d.th_d = a.take<double>((size_t)L.total_bins * L.P_max);
+    d.th_sd = a.take<double>((size_t)L.total_bins * L.P_max);
+    d.status = a.take<unsigned int>(4);
+    d.counters = a.take<unsigned long long>(8);
+    const int iof = std::max(IO_FLOATS_MIN, 8 * L.max_n);
+    *io = a.take<float>(iof);
+    *io_floats = iof;
+    return (a.off + ALIGN - 1) / ALIGN * ALIGN;
+}
+
+}  // namespace
+
+struct la_handle {
+    Layout L;
+    Dev d{};
+    HostView hv{};
+    std::vector<SysDev> sys;
+    std::vector<WalkerDev> walk;
+    std::vector<StageDev> stages;
+    std::vector<int> slot_off, slot_cap, sc_cap, n_cols, alch_base, n_alch, item_cap, bo_off, n_bo;
+    std::vector<int> sys_w0;       // first walker of each system
+    std::vector<int> sys_stage0;   // first stage of each system
+    std::vector<int> sys_nstage;
+    void *io = nullptr;
+    int io_floats = 0;
+    la_options opt{};
+    int graph_steps = 10;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int n_sm = 0;
+    unsigned *h_status = nullptr;  // pinned
+    cudaEvent_t status_ev = nullptr;
+    int sticky = LA_OK;
+    long long steps = 0, launches = 0, launches_per_step = 0;
+    std::string err, report;
+};
+
+namespace {
+
+int fail(la_handle *h, int code, const char *fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return code;
+}
+
+#define CU(h, call)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) return fail(h, LA_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+int status_to_code(unsigned bits) {
+    if (bits & (LA_STATUS_LIST_OVERFLOW | LA_STATUS_COLUMN_OVERFLOW | LA_STATUS_ALCH_OVERFLOW))
+        return LA_ERR_LIST_OVERFLOW;
+    if (bits & LA_STATUS_FIXED_OVERFLOW) return LA_ERR_FIXED_OVERFLOW;
+    if (bits & LA_STATUS_NONFINITE) return LA_ERR_NONFINITE;
+    return LA_OK;
+}
+
+const char *status_text(unsigned bits) {
+    if (bits & LA_STATUS_COLUMN_OVERFLOW) return "a neighbour-search column exceeded 2048 atoms";
+    if (bits & LA_STATUS_ALCH_OVERFLOW) return "an alchemical pair list exceeded its capacity";
+    if (bits & LA_STATUS_LIST_OVERFLOW) return "the cluster-pair list exceeded its capacity";
+    if (bits & LA_STATUS_FIXED_OVERFLOW) return "a force exceeded the fixed-point range";
+    if (bits & LA_STATUS_NONFINITE) return "non-finite positions or lambda";
+    return "ok";
+}
+
+// enqueue a copy of the status word to pinned memory after the call's work
+void post_status(la_handle *h, cudaStream_t s) {
+    cudaMemcpyAsync(h->h_status, h->d.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(h->status_ev, s);
+}
+
+int check_posted(la_handle *h) {
+    if (h->sticky != LA_OK) return fail(h, LA_ERR_STATE, "handle in error state: %s", h->err.c_str());
+    if (cudaEventQuery(h->status_ev) == cudaSuccess && *h->h_status) {
+        int code = status_to_code(*h->h_status);
+        if (code != LA_OK) {
+            h->sticky = code;
+            return fail(h, LA_ERR_STATE, "device error: %s", status_text(*h->h_status));
+        }
+    }
+    return LA_OK;
+}
+
+int sync_status(la_handle *h, cudaStream_t s, unsigned *bits) {
+    CU(h, cudaStreamSynchronize(s));
+    unsigned st = 0;
+    CU(h, cudaMemcpy(&st, h->d.status, sizeof st, cudaMemcpyDeviceToHost));
+    if (bits) *bits = st;
+    int code = status_to_code(st);
+    if (code != LA_OK) {
+        h->sticky = code;
+        return fail(h, code, "device error: %s", status_text(st));
+    }
+    return LA_OK;
+}
+
+// one batched MD step over walkers [w0, w1)
+int enqueue_step(la_handle *h, int w0, int w1, cudaStream_t s) {
+    launch_integrate(h->d, h->hv, w0, w1, s);
+    launch_rebuild(h->d, h->hv, w0, w1, s);
+    launch_pairs(h->d, h->hv, w0, w1, false, s);
+    launch_bonded(h->d, h->hv, w0, w1, false, s);
+    launch_walker(h->d, w0, w1, false, s);
+    launch_lambda(h->d, 0, (int)h->stages.size(), false, s);
+    return 0;
+}
+
+int kernels_per_step(la_handle *h) {
+    int n = 1 + rebuild_kernel_count(h->hv, 0, h->L.W) + 1 + 1 + 1;
+    const int nbo = h->hv.bo_off[h->L.W - 1] + h->hv.n_bo[h->L.W - 1];
+    if (nbo > 0) ++n;
+    return n;
+}
+
+// evaluate forces, dU/dlambda and G at the current state of walkers [w0, w1)
+int prime(la_handle *h, int w0, int w1, bool force_rebuild, bool energy, cudaStream_t s) {
+    if (force_rebuild) {
+        std::vector<int> one(w1 - w0, 1);
+        CU(h, cudaMemcpyAsync(h->d.rebuild + w0, one.data(), sizeof(int) * one.size(),
+                              cudaMemcpyHostToDevice, s));
+        CU(h, cudaStreamSynchronize(s));
+    }
+    const size_t g0 = h->slot_off[w0], g1 = (size_t)h->slot_off[w1 - 1] + h->slot_cap[w1 - 1];
+    CU(h, cudaMemsetAsync(h->d.F + 3 * g0, 0, 3 * (g1 - g0) * sizeof(unsigned long long), s));
+    if (energy) CU(h, cudaMemsetAsync(h->d.eterm + (size_t)N_ETERMS * w0, 0,
+                                      sizeof(long long) * N_ETERMS * (w1 - w0), s));
+    launch_rebuild(h->d, h->hv, w0, w1, s);
+    launch_pairs(h->d, h->hv, w0, w1, energy, s);
+    launch_bonded(h->d, h->hv, w0, w1, energy, s);
+    launch_walker(h->d, w0, w1, energy, s);
+    launch_lambda(h->d, 0, (int)h->stages.size(), true, s);
+    h->launches += 4 + rebuild_kernel_count(h->hv, w0, w1);
+    CU(h, cudaGetLastError());
+    return LA_OK;
+}
+
+int capture_graph(la_handle *h) {
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    cudaGraph_t g;
+    CU(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < h->graph_steps; ++k) enqueue_step(h, 0, h->L.W, h->cap_stream);
+    CU(h, cudaStreamEndCapture(h->cap_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, LA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    h->launches_per_step = kernels_per_step(h);
+    return LA_OK;
+}
+
+void set_pair_blocks(la_handle *h, int ctas_per_sm) {
+    h->hv.pair_blocks = std::max(1, ctas_per_sm) * h->n_sm;
+}
+
+int time_steps(la_handle *h, int n, cudaStream_t s, float *ms) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    for (int k = 0; k < n; ++k) enqueue_step(h, 0, h->L.W, s);
+    cudaEventRecord(b, s);
+    cudaError_t e = cudaEventSynchronize(b);
+    cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return e == cudaSuccess ? LA_OK : fail(h, LA_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+}
+
+std::map<std::string, std::pair<int, int>> &tune_cache() {
+    static std::map<std::string, std::pair<int, int>> c;
+    return c;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int la_query_sizes(const la_system_desc *sys, int n_sys, const la_options *opt, size_t *arena_bytes) {
+    std::string err;
+    int rc = validate(sys, n_sys, err);
+    if (rc != LA_OK) return rc;
+    if (!arena_bytes) return LA_ERR_INVALID_ARG;
+    Layout L;
+    compute_layout(sys, n_sys, opt, L);
+    Dev d{};
+    void *io;
+    int iof;
+    SysDev *a;
+    WalkerDev *b;
+    StageDev *c;
+    *arena_bytes = carve(L, nullptr, 0, d, &io, &iof, &a, &b, &c);
+    return LA_OK;
+}
+
+int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt, void *arena,
+                     size_t arena_bytes, void *stream, la_handle **out) {
+    if (!out) return LA_ERR_INVALID_ARG;
+    *out = nullptr;
+    la_handle *h = new la_handle();
+    std::string err;
+    int rc = validate(sys, n_sys, err);
+    if (rc != LA_OK) {
+        h->err = err;
+        *out = h;
+        return rc;
+    }
+    if (opt) h->opt = *opt;
+    compute_layout(sys, n_sys, opt, h->L);
+    const Layout &L = h->L;
+    cudaStream_t s = (cudaStream_t)stream;
+    SysDev *d_sys;
+    WalkerDev *d_walk;
+    StageDev *d_stage;
+    size_t need = carve(L, (char *)arena, arena_bytes, h->d, &h->io, &h->io_floats, &d_sys, &d_walk, &d_stage);
+    *out = h;
+    if (!arena || need > arena_bytes || ((uintptr_t)arena % ALIGN) != 0)
+        return fail(h, LA_ERR_ARENA_TOO_SMALL, "arena of %zu bytes (need %zu, 256-byte aligned)", arena_bytes, need);
+    int dev;
+    CU(h, cudaGetDevice(&dev));
+    CU(h, cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
+
+    Dev &d = h->d;
+    d.n_sys = n_sys;
+    d.n_walkers = L.W;
+    d.n_stages = L.n_stages;
+    d.ent_cap = L.ent_cap;
+    d.alch_cap = L.alch_cap;
+    d.max_bins = L.max_bins;
+    d.P_max = L.P_max;
+    d.chunk = L.chunk;
+    d.sys = d_sys;
+    d.walk = d_walk;
+    d.stage = d_stage;
+
+    // ---- per-system static data ----
+    std::vector<float4> ap(L.atoms_s);
+    std::vector<float> an(L.atoms_s);
+    std::vector<int> ag(L.atoms_s), alch_atoms;
+    std::vector<int4> ax(L.atoms_s);
+    std::vector<unsigned char> aa(L.atoms_s);
+    std::vector<int2> bij;
+    std::vector<float2> bp, angp;
+    std::vector<int4> aijk;
+    std::vector<int> pidx, fbidx, lhidx;
+    std::vector<float4> px0, lhx0;
+    int atom_off = 0, alch_off = 0, stage_idx = 0, bin_off = 0;
+    int w_glob = 0;
+    long long slot_off = 0, sc_off = 0, col_off = 0, atom_base = 0, alch_base = 0, item_base = 0, bo = 0;
+    const int chunks = (L.ent_cap + L.chunk - 1) / L.chunk;
+    std::vector<float4> xq0(L.slots), vv0(L.slots);
+    std::vector<float2> lj0(L.slots), im0(L.slots);
+    std::vector<int> aos0(L.slots, -1), sw0(L.slots), soa0(L.atoms_w);
+    std::vector<double> lam0(L.W), plam0(L.W);
+    for (int si = 0; si < n_sys; ++si) {
+        const la_system_desc &S = sys[si];
+        const SysLayout &sl = L.sys[si];
+        SysDev D{};
+        D.n_atoms = S.n_atoms;
+        D.atom_off = atom_off;
+        D.n_alch = sl.n_alch;
+        D.alch_off = alch_off;
+        D.P = sl.P;
+        D.box = S.box;
+        D.box_inv = 1.0 / S.box;
+        D.boxf = (float)S.box;
+        D.box_invf = (float)(1.0 / S.box);
+        D.rc2 = (float)(S.r_cut * S.r_cut);
+        const double rc = S.r_cut;
+        const double krf = S.eps_rf <= 0.0 ? 1.0 / (2.0 * rc * rc * rc)
+                                           : (S.eps_rf - 1.0) / ((2.0 * S.eps_rf + 1.0) * rc * rc * rc);
+        D.krf = (float)krf;
+        D.crf = (float)(1.0 / rc + krf * rc * rc);
+        D.sqrt_coul = (float)std::sqrt(std::max(0.0, S.coul));
+        D.b_v = S.b_v;
+        D.b_e = S.b_e;
+        D.sc_alpha = (float)S.sc_alpha;
+        D.sc_n = S.sc_n;
+        D.sc_m = S.sc_m;
+        D.dt = (float)S.dt;
+        const double c_at = std::exp(-S.gamma * S.dt);
+        D.c_at = (float)c_at;
+        D.s_at = (float)std::sqrt(std::max(0.0, 1.0 - c_at * c_at));
+        D.dt_d = S.dt;
+        D.m_lambda = S.m_lambda;
+        D.c_lm = std::exp(-S.gamma_lambda * S.dt);
+        D.sd_lm = std::sqrt(std::max(0.0, (1.0 - D.c_lm * D.c_lm) * S.m_lambda * S.kT));
+        D.kT = S.kT;
+        D.half_skin2 = (float)(0.25 * S.skin * S.skin);
+        const double binv = 1.0 / S.box;
+        const double a_ = sl.r_list * binv;
+        D.R = (long long)std::floor((a_ * a_) * 281474976710656.0);
+        D.Rq = (int)std::ceil(a_ * 16777216.0) + 1;
+        D.ncx = sl.ncx;
+        D.bond_off = (int)bij.size();
+        D.n_bonds = S.n_bonds;
+        for (int b = 0; b < S.n_bonds; ++b) {
+            bij.push_back(make_int2(S.bond_ij[2 * b], S.bond_ij[2 * b + 1]));
+            bp.push_back(make_float2((float)S.bond_r0[b], (float)S.bond_k[b]));
+        }
+        D.angle_off = (int)aijk.size();
+        D.n_angles = S.n_angles;
+        for (int b = 0; b < S.n_angles; ++b) {
+            aijk.push_back(make_int4(S.angle_ijk[3 * b], S.angle_ijk[3 * b + 1], S.angle_ijk[3 * b + 2], 0));
+            angp.push_back(make_float2((float)S.angle_t0[b], (float)S.angle_k[b]));
+        }
+        D.posres_off = (int)pidx.size();
+        D.n_posres = S.n_posres;
+        D.posres_k = (float)S.posres_k;
+        for (int b = 0; b < S.n_posres; ++b) {
+            pidx.push_back(S.posres_idx[b]);
+            px0.push_back(make_float4((float)S.posres_x0[3 * b], (float)S.posres_x0[3 * b + 1],
+                                      (float)S.posres_x0[3 * b + 2], 0.f));
+        }
+        D.fb_off = (int)fbidx.size();
+        D.n_fb_a = S.n_fb_a;
+        D.n_fb_b = S.n_fb_b;
+        D.fb_d0 = (float)S.fb_d0;
+        D.fb_k = (float)S.fb_k;
+        for (int b = 0; b < S.n_fb_a; ++b) fbidx.push_back(S.fb_a[b]);
+        for (int b = 0; b < S.n_fb_b; ++b) fbidx.push_back(S.fb_b[b]);
+        D.lh_off = (int)lhidx.size();
+        D.n_lh = S.n_lh;
+        D.lh_dims = S.lh_dims;
+        D.lh_k0 = S.lh_k0;
+        D.lh_k1 = S.lh_k1;
+        for (int b = 0; b < S.n_lh; ++b) {
+            lhidx.push_back(S.lh_idx[b]);
+            lhx0.push_back(make_float4((float)S.lh_x0[3 * b], (float)S.lh_x0[3 * b + 1],
+                                       (float)S.lh_x0[3 * b + 2], 0.f));
+        }
+        D.seed = S.seed;
+        D.lambda_dynamics = S.lambda_dynamics;
+        D.abf_on = S.abf_on;
+        D.theta_stats = S.theta_stats;
+        D.shared_freq = S.shared_freq > 0 ? S.shared_freq : 1;
+        D.n_full = S.n_full;
+        h->sys.push_back(D);
+        const double sqc = std::sqrt(std::max(0.0, S.coul));
+        for (int i = 0; i < S.n_atoms; ++i) {
+            ap[atom_off + i] = make_float4((float)(S.charge[i] * sqc), (float)(0.5 * S.sigma[i]),
+                                           (float)(2.0 * std::sqrt(std::max(0.0, S.epsilon[i]))),
+                                           (float)(1.0 / S.mass[i]));
+            an[atom_off + i] = (float)std::sqrt(S.kT / S.mass[i]);
+            ag[atom_off + i] = S.excl_group[i];
+            ax[atom_off + i] = make_int4(S.excl_extra[4 * i], S.excl_extra[4 * i + 1], S.excl_extra[4 * i + 2],
+                                         S.excl_extra[4 * i + 3]);
+            aa[atom_off + i] = S.alch[i] ? 1 : 0;
+            if (S.alch[i]) alch_atoms.push_back(i);
+        }
+        // stages and walkers
+        h->sys_w0.push_back(w_glob);
+        h->sys_stage0.push_back(stage_idx);
+        h->sys_nstage.push_back(S.n_stages);
+        int wl = 0;
+        for (int k = 0; k < S.n_stages; ++k) {
+            StageDev st{};
+            st.sys = si;
+            st.w0 = w_glob;
+            st.w1 = w_glob + S.stage_walkers[k];
+            st.n_bins = S.stage_bins[k];
+            st.bin_off = bin_off;
+            st.lo = S.stage_lo[k];
+            st.hi = S.stage_hi[k];
+            st.width = (st.hi - st.lo) / st.n_bins;
+            bin_off += st.n_bins;
+            for (int q = 0; q < S.stage_walkers[k]; ++q) {
+                WalkerDev W{};
+                W.sys = si;
+                W.stage = stage_idx;
+                W.wlocal = wl;
+                W.slot_off = (int)slot_off;
+                W.sc_cap = sl.sc_cap;
+                W.sc_off = (int)sc_off;
+                W.col_off = (int)col_off;
+                W.n_cols = sl.n_cols;
+                W.atom_base = (int)atom_base;
+                W.alch_base = (int)alch_base;
+                W.item_base = (int)item_base;
+                W.item_cap = sl.sc_cap * chunks;
+                W.bo_off = (int)bo;
+                W.n_bo = S.n_bonds + S.n_angles + S.n_posres;
+                // initial layout: slot = atom index, padding beyond
+                const float *x = S.x0 + (size_t)wl * S.n_atoms * 3;
+                const float *v = S.v0 + (size_t)wl * S.n_atoms * 3;
+                for (int i = 0; i < sl.slot_cap; ++i) {
+                    const size_t g = slot_off + i;
+                    sw0[g] = w_glob;
+                    if (i < S.n_atoms) {
+                        xq0[g] = make_float4(x[3 * i], x[3 * i + 1], x[3 * i + 2], ap[atom_off + i].x);
+                        vv0[g] = make_float4(v[3 * i], v[3 * i + 1], v[3 * i + 2], 0.f);
+                        lj0[g] = make_float2(ap[atom_off + i].y, ap[atom_off + i].z);
+                        im0[g] = make_float2(ap[atom_off + i].w, an[atom_off + i]);
+                        aos0[g] = i;
+                        soa0[atom_base + i] = (int)g;
+                    } else {
+                        xq0[g] = make_float4(x[0], x[1], x[2], 0.f);
+                    }
+                }
+                lam0[w_glob] = S.lam0[wl];
+                plam0[w_glob] = S.plam0[wl];
+                h->walk.push_back(W);
+                h->slot_off.push_back(W.slot_off);
+                h->slot_cap.push_back(sl.slot_cap);
+                h->sc_cap.push_back(sl.sc_cap);
+                h->n_cols.push_back(sl.n_cols);
+                h->alch_base.push_back(W.alch_base);
+                h->n_alch.push_back(sl.n_alch);
+                h->item_cap.push_back(W.item_cap);
+                h->bo_off.push_back(W.bo_off);
+                h->n_bo.push_back(W.n_bo);
+                slot_off += sl.slot_cap;
+                sc_off += sl.sc_cap;
+                col_off += sl.n_cols;
+                atom_base += sl.n;
+                alch_base += sl.n_alch;
+                item_base += W.item_cap;
+                bo += W.n_bo;
+                ++w_glob;
+                ++wl;
+            }
+            h->stages.push_back(st);
+            ++stage_idx;
+        }
+        atom_off += S.n_atoms;
+        alch_off += sl.n_alch;
+    }
+    d.total_bo = (int)bo;
+    auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+        if (!bytes) return cudaSuccess;
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    // (re)load the whole initial state; also used to undo the autotuner's steps
+    auto upload = [&]() -> int {
+    CU(h, cudaMemsetAsync(arena, 0, need, s));
+    CU(h, up(d_sys, h->sys.data(), sizeof(SysDev) * h->sys.size()));
+    CU(h, up(d_walk, h->walk.data(), sizeof(WalkerDev) * h->walk.size()));
+    CU(h, up(d_stage, h->stages.data(), sizeof(StageDev) * h->stages.size()));
+    CU(h, up((void *)d.ap, ap.data(), sizeof(float4) * ap.size()));
+    CU(h, up((void *)d.aparam_mut, ap.data(), sizeof(float4) * ap.size()));
+    CU(h, up((void *)d.anoise, an.data(), sizeof(float) * an.size()));
+    CU(h, up((void *)d.agroup, ag.data(), sizeof(int) * ag.size()));
+    CU(h, up((void *)d.aexcl, ax.data(), sizeof(int4) * ax.size()));
+    CU(h, up((void *)d.aalch, aa.data(), aa.size()));
+    CU(h, up((void *)d.alch_atoms, alch_atoms.data(), sizeof(int) * alch_atoms.size()));
+    CU(h, up((void *)d.bond_ij, bij.data(), sizeof(int2) * bij.size()));
+    CU(h, up((void *)d.bond_p, bp.data(), sizeof(float2) * bp.size()));
+    CU(h, up((void *)d.angle_ijk, aijk.data(), sizeof(int4) * aijk.size()));
+    CU(h, up((void *)d.angle_p, angp.data(), sizeof(float2) * angp.size()));
+    CU(h, up((void *)d.posres_idx, pidx.data(), sizeof(int) * pidx.size()));
+    CU(h, up((void *)d.posres_x0, px0.data(), sizeof(float4) * px0.size()));
+    CU(h, up((void *)d.fb_idx, fbidx.data(), sizeof(int) * fbidx.size()));
+    CU(h, up((void *)d.lh_idx, lhidx.data(), sizeof(int) * lhidx.size()));
+    CU(h, up((void *)d.lh_x0, lhx0.data(), sizeof(float4) * lhx0.size()));
+    CU(h, up(d.xq, xq0.data(), sizeof(float4) * xq0.size()));
+    CU(h, up(d.vv, vv0.data(), sizeof(float4) * vv0.size()));
+    CU(h, up(d.xref, xq0.data(), sizeof(float4) * xq0.size()));
+    CU(h, up(d.lj, lj0.data(), sizeof(float2) * lj0.size()));
+    CU(h, up(d.im, im0.data(), sizeof(float2) * im0.size()));
+    CU(h, up(d.atom_of_slot, aos0.data(), sizeof(int) * aos0.size()));
+    CU(h, up(d.slot_walker, sw0.data(), sizeof(int) * sw0.size()));
+    CU(h, up(d.slot_of_atom, soa0.data(), sizeof(int) * soa0.size()));
+    CU(h, up(d.lam, lam0.data(), sizeof(double) * lam0.size()));
+    CU(h, up(d.plam, plam0.data(), sizeof(double) * plam0.size()));
+    CU(h, cudaStreamSynchronize(s));
+    return LA_OK;
+    };
+    rc = upload();
+    if (rc != LA_OK) return rc;
+
+    HostView &hv = h->hv;
+    hv.n_walkers = L.W;
+    hv.n_sm = h->n_sm;
+    hv.slot_off = h->slot_off.data();
+    hv.slot_cap = h->slot_cap.data();
+    hv.sc_cap = h->sc_cap.data();
+    hv.n_cols = h->n_cols.data();
+    hv.alch_base = h->alch_base.data();
+    hv.n_alch = h->n_alch.data();
+    hv.item_cap = h->item_cap.data();
+    hv.bo_off = h->bo_off.data();
+    hv.n_bo = h->n_bo.data();
+    set_pair_blocks(h, h->opt.pair_ctas_per_sm > 0 ? h->opt.pair_ctas_per_sm : 4);
+    h->graph_steps = h->opt.graph_steps > 0 ? h->opt.graph_steps : 10;
+
+    CU(h, cudaMallocHost((void **)&h->h_status, sizeof(unsigned)));
+    *h->h_status = 0;
+    CU(h, cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming));
+    CU(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+
+    rc = prime(h, 0, L.W, true, false, s);
+    if (rc != LA_OK) return rc;
+    rc = sync_status(h, s, nullptr);
+    if (rc != LA_OK) return rc;
+
+    // ---- launch-shape autotuner: CTAs per SM of the pair kernel, entries per item ----
+    char rep[512];
+    if (h->opt.autotune) {
+        char key[256];
+        snprintf(key, sizeof key, "dev%d-sm%d-W%d-slots%lld-ent%d", dev, h->n_sm, L.W, L.slots, L.ent_cap);
+        auto it = tune_cache().find(key);
+        int best_c = 4, best_k = L.chunk;
+        if (it != tune_cache().end()) {
+            best_c = it->second.first;
+            best_k = it->second.second;
+        } else {
+            // timing advances the walkers: the initial state is re-loaded after
+            float best = 1e30f;
+            const int ctas[] = {2, 3, 4, 6, 8};
+            const int chunksz[] = {16, 32, 64};
+            for (int k : chunksz) {
+                if ((L.ent_cap + k - 1) / k * k < L.chunk) continue;
+                if (k < L.chunk) continue;  // item capacity was sized for L.chunk
+                d.chunk = k;
+                for (int c : ctas) {
+                    set_pair_blocks(h, c);
+                    rc = prime(h, 0, L.W, true, false, s);
+                    if (rc != LA_OK) return rc;
+                    float ms = 0.f;
+                    rc = time_steps(h, 2, s, &ms);  // warm
+                    if (rc != LA_OK) return rc;
+                    rc = time_steps(h, 6, s, &ms);
+                    if (rc != LA_OK) return rc;
+                    if (ms < best) {
+                        best = ms;
+                        best_c = c;
+                        best_k = k;
+                    }
+                }
+            }
+            tune_cache()[key] = {best_c, best_k};
+        }
+        d.chunk = best_k;
+        set_pair_blocks(h, best_c);
+        rc = upload();
+        if (rc != LA_OK) return rc;
+        h->steps = 0;
+        rc = prime(h, 0, L.W, true, false, s);
+        if (rc != LA_OK) return rc;
+        snprintf(rep, sizeof rep, "autotuned: pair CTAs/SM=%d, entries/item=%d, warps/CTA=8, graph steps=%d",
+                 best_c, best_k, h->graph_steps);
+    } else {
+        snprintf(rep, sizeof rep, "default: pair CTAs/SM=%d, entries/item=%d, warps/CTA=8, graph steps=%d",
+                 h->hv.pair_blocks / h->n_sm, d.chunk, h->graph_steps);
+    }
+    h->report = rep;
+    rc = capture_graph(h);
+    if (rc != LA_OK) return rc;
+    return sync_status(h, s, nullptr);
+}
+
+int la_step_walkers(la_handle *h, int64_t n_steps, void *stream) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    if (n_steps < 0) return fail(h, LA_ERR_INVALID_ARG, "n_steps < 0");
+    int rc = check_posted(h);
+    if (rc != LA_OK) return rc;
+    if (n_steps == 0) return LA_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t reps = n_steps / h->graph_steps, rem = n_steps % h->graph_steps;
+    for (int64_t r = 0; r < reps; ++r) CU(h, cudaGraphLaunch(h->graph, s));
+    for (int64_t r = 0; r < rem; ++r) enqueue_step(h, 0, h->L.W, s);
+    launch_finish(h->d, h->hv, 0, h->L.W, s);
+    CU(h, cudaGetLastError());
+    h->steps += n_steps;
+    h->launches += n_steps * h->launches_per_step + 1;
+    post_status(h, s);
+    return LA_OK;
+}
+
+int la_step_walkers_plain(la_handle *h, int64_t n_steps, void *stream) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    if (n_steps < 0) return fail(h, LA_ERR_INVALID_ARG, "n_steps < 0");
+    int rc = check_posted(h);
+    if (rc != LA_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int W = h->L.W;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        for (int w = 0; w < W; ++w) {
+            launch_integrate(h->d, h->hv, w, w + 1, s);
+            launch_rebuild(h->d, h->hv, w, w + 1, s);
+            launch_pairs(h->d, h->hv, w, w + 1, false, s);
+            launch_bonded(h->d, h->hv, w, w + 1, false, s);
+            launch_walker(h->d, w, w + 1, false, s);
+            h->launches += 3 + rebuild_kernel_count(h->hv, w, w + 1) + (h->n_bo[w] > 0 ? 1 : 0);
+        }
+        launch_lambda(h->d, 0, (int)h->stages.size(), false, s);
+        h->launches += 1;
+    }
+    if (n_steps > 0) {
+        for (int w = 0; w < W; ++w) launch_finish(h->d, h->hv, w, w + 1, s);
+        h->launches += W;
+    }
+    CU(h, cudaGetLastError());
+    h->steps += n_steps;
+    post_status(h, s);
+    return LA_OK;
+}
+
+int la_read_abf(la_handle *h, int sys, int stage, double *sum, double *sumsq, int64_t *count, double *grad,
+                double *A, double *dA, double *dA_se, void *stream) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    if (sys < 0 || sys >= (int)h->sys.size() || stage < 0 || stage >= h->sys_nstage[sys])
+        return fail(h, LA_ERR_INVALID_ARG, "bad system/stage");
+    cudaStream_t s = (cudaStream_t)stream;
+    const StageDev &st = h->stages[h->sys_stage0[sys] + stage];
+    const int nb = st.n_bins;
+    std::vector<double> s1(nb), s2(nb);
+    std::vector<unsigned long long> c(nb);
+    CU(h, cudaMemcpyAsync(s1.data(), h->d.abf_sum + st.bin_off, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(s2.data(), h->d.abf_sumsq + st.bin_off, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(c.data(), h->d.abf_count + st.bin_off, sizeof(unsigned long long) * nb,
+                          cudaMemcpyDeviceToHost, s));
+    int rc = sync_status(h, s, nullptr);
+    if (rc != LA_OK) return rc;
+    // TI read-out (Sec. 2.3): Riemann sum of bin means
+    const double w = st.width;
+    double acc = 0.0, var_acc = 0.0;
+    bool empty = false;
+    if (A) A[0] = 0.0;
+    for (int k = 0; k < nb; ++k) {
+        if (sum) sum[k] = s1[k];
+        if (sumsq) sumsq[k] = s2[k];
+        if (count) count[k] = (int64_t)c[k];
+        double g = std::nan("");
+        if (c[k] > 0) {
+            g = s1[k] / (double)c[k];
+            const double var = std::max(0.0, s2[k] / (double)c[k] - g * g);
+            var_acc += var / (double)c[k];
+        } else {
+            empty = true;
+        }
+        if (grad) grad[k] = g;
+        acc += w * g;
+        if (A) A[k + 1] = acc;
+    }
+    if (dA) *dA = acc;
+    if (dA_se) *dA_se = empty ? std::nan("") : w * std::sqrt(var_acc);
+    return empty ? LA_WARN_EMPTY_BIN : LA_OK;
+}
+
+int la_energy_forces(la_handle *h, int walker, uint32_t flags, double *energy_terms, float *forces, double *dUdl,
+                     double *dUdtheta, double *d2Udl_dtheta, void *stream) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    if (walker < 0 || walker >= h->L.W) return fail(h, LA_ERR_INVALID_ARG, "bad walker");
+    if (h->sticky != LA_OK) return fail(h, LA_ERR_STATE, "handle in error state: %s", h->err.c_str());
+    cudaStream_t s = (cudaStream_t)stream;
+    if (flags & LA_EF_COUNT_PAIRS) CU(h, cudaMemsetAsync(h->d.counters + 1, 0, 2 * sizeof(unsigned long long), s));
+    int rc = prime(h, walker, walker + 1, (flags & LA_EF_REBUILD) != 0, true, s);
+    if (rc != LA_OK) return rc;
+    const WalkerDev &W = h->walk[walker];
+    const SysDev &S = h->sys[W.sys];
+    if (forces) launch_forces_out(h->d, walker, S.n_atoms, forces, s);
+    long long et[N_ETERMS];
+    double sw = 0.0;
+    std::vector<double> th(2 * h->L.P_max);
+    CU(h, cudaMemcpyAsync(et, h->d.eterm + (size_t)N_ETERMS * walker, sizeof et, cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(&sw, h->d.s + walker, sizeof sw, cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(th.data(), h->d.wth + (size_t)walker * 2 * h->L.P_max, sizeof(double) * th.size(),
+                          cudaMemcpyDeviceToHost, s));
+    rc = sync_status(h, s, nullptr);
+    if (rc != LA_OK) return rc;
+    if (energy_terms)
+        for (int k = 0; k < LA_N_TERMS; ++k) energy_terms[k] = (double)et[k] / E_TO_FIX;
+    if (dUdl) *dUdl = sw;
+    for (int p = 0; p < S.P; ++p) {
+        if (dUdtheta) dUdtheta[p] = th[p];
+        if (d2Udl_dtheta) d2Udl_dtheta[p] = th[h->L.P_max + p];
+    }
+    return LA_OK;
+}
+
+int la_get_state(la_handle *h, int walker, float *x, float *v, double *lam, double *plam, uint64_t *step,
+                 void *stream) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    if (walker < 0 || walker >= h->L.W) return fail(h, LA_ERR_INVALID_ARG, "bad walker");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = h->sys[h->walk[walker].sys].n_atoms;
+    float *io = (float *)h->io;
+    launch_state_io(h->d, walker, n, io, io + 3 * (size_t)n, false, s);
+    std::vector<float> buf(6 * (size_t)n);
+    CU(h, cudaMemcpyAsync(buf.data(), io, sizeof(float) * buf.size(), cudaMemcpyDeviceToHost, s));
+    double l = 0, p = 0;
+    unsigned long long st = 0;
+    CU(h, cudaMemcpyAsync(&l, h->d.lam + walker, sizeof l, cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(&p, h->d.plam + walker, sizeof p, cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(&st, h->d.step + walker, sizeof st, cudaMemcpyDeviceToHost, s));
+    CU(h, cudaStreamSynchronize(s));
+    if (x) memcpy(x, buf.data(), sizeof(float) * 3 * n);
+    if (v) memcpy(v, buf.data() + 3 * (size_t)n, sizeof(float) * 3 * n);
+    if (lam) *lam = l;
+    if (plam) *plam = p;
+    if (step) *step = st;
+    return LA_OK;
+}
+
+int la_set_state(la_handle *h, int walker, const float *x, const float *v, const double *lam, const double *plam,
+                 void *stream) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    if (walker < 0 || walker >= h->L.W) return fail(h, LA_ERR_INVALID_ARG, "bad walker");
+    if (h->sticky != LA_OK) return fail(h, LA_ERR_STATE, "handle in error state: %s", h->err.c_str());
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = h->sys[h->walk[walker].sys].n_atoms;
+    float *io = (float *)h->io;
+    // read back the current state so that NULL fields stay unchanged
+    launch_state_io(h->d, walker, n, io, io + 3 * (size_t)n, false, s);
+    if (x) CU(h, cudaMemcpyAsync(io, x, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+    if (v) CU(h, cudaMemcpyAsync(io + 3 * (size_t)n, v, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+    launch_state_io(h->d, walker, n, io, io + 3 * (size_t)n, true, s);
+    if (lam) CU(h, cudaMemcpyAsync(h->d.lam + walker, lam, sizeof(double), cudaMemcpyHostToDevice, s));
+    if (plam) CU(h, cudaMemcpyAsync(h->d.plam + walker, plam, sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(h, cudaStreamSynchronize(s));
+    int rc = prime(h, walker, walker + 1, true, false, s);
+    if (rc != LA_OK) return rc;
+    return sync_status(h, s, nullptr);
+}
+
+int la_set_alch_params(la_handle *h, int sys, const double *theta, void *stream) {
+    if (!h || !theta) return LA_ERR_INVALID_ARG;
+    if (sys < 0 || sys >= (int)h->sys.size()) return fail(h, LA_ERR_INVALID_ARG, "bad system");
+    cudaStream_t s = (cudaStream_t)stream;
+    const SysDev &S = h->sys[sys];
+    std::vector<int> idx(S.n_alch);
+    CU(h, cudaMemcpy(idx.data(), h->d.alch_atoms + S.alch_off, sizeof(int) * S.n_alch, cudaMemcpyDeviceToHost));
+    std::vector<float4> ap(S.n_atoms);
+    CU(h, cudaMemcpy(ap.data(), h->d.aparam_mut + S.atom_off, sizeof(float4) * S.n_atoms, cudaMemcpyDeviceToHost));
+    for (int r = 0; r < S.n_alch; ++r) {
+        const double eps = theta[3 * r], sig = theta[3 * r + 1], q = theta[3 * r + 2];
+        if (!(eps >= 0) || !(sig >= 0)) return fail(h, LA_ERR_INVALID_ARG, "negative epsilon or sigma");
+        float4 &p = ap[idx[r]];
+        p.x = (float)(q * S.sqrt_coul);
+        p.y = (float)(0.5 * sig);
+        p.z = (float)(2.0 * std::sqrt(eps));
+    }
+    CU(h, cudaMemcpyAsync(h->d.aparam_mut + S.atom_off, ap.data(), sizeof(float4) * S.n_atoms,
+                          cudaMemcpyHostToDevice, s));
+    const int w0 = h->sys_w0[sys];
+    int w1 = w0;
+    while (w1 < h->L.W && h->walk[w1].sys == sys) ++w1;
+    int rc = prime(h, w0, w1, true, false, s);
+    if (rc != LA_OK) return rc;
+    return sync_status(h, s, nullptr);
+}
+
+int la_read_theta(la_handle *h, int sys, int stage, double *sum_d2, double *sum_d, double *sum_sd, void *stream) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    if (sys < 0 || sys >= (int)h->sys.size() || stage < 0 || stage >= h->sys_nstage[sys])
+        return fail(h, LA_ERR_INVALID_ARG, "bad system/stage");
+    cudaStream_t s = (cudaStream_t)stream;
+    const StageDev &st = h->stages[h->sys_stage0[sys] + stage];
+    const int P = h->sys[sys].P, PM = h->L.P_max;
+    std::vector<double> buf((size_t)st.n_bins * PM);
+    double *outs[3] = {sum_d2, sum_d, sum_sd};
+    double *srcs[3] = {h->d.th_d2, h->d.th_d, h->d.th_sd};
+    for (int q = 0; q < 3; ++q) {
+        if (!outs[q]) continue;
+        CU(h, cudaMemcpyAsync(buf.data(), srcs[q] + (size_t)st.bin_off * PM, sizeof(double) * buf.size(),
+                              cudaMemcpyDeviceToHost, s));
+        CU(h, cudaStreamSynchronize(s));
+        for (int k = 0; k < st.n_bins; ++k)
+            for (int p = 0; p < P; ++p) outs[q][(size_t)k * P + p] = buf[(size_t)k * PM + p];
+    }
+    return LA_OK;
+}
+
+int la_get_pairs(la_handle *h, int walker, int32_t *pairs, uint8_t *kind, int64_t cap, int64_t *count,
+                 void *stream) {
+    if (!h || !count) return LA_ERR_INVALID_ARG;
+    if (walker < 0 || walker >= h->L.W) return fail(h, LA_ERR_INVALID_ARG, "bad walker");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(h, cudaStreamSynchronize(s));
+    const WalkerDev &W = h->walk[walker];
+    const SysDev &S = h->sys[W.sys];
+    const int nslot = h->slot_cap[walker];
+    std::vector<int> aos(nslot), nent(W.sc_cap);
+    int nsc = 0;
+    CU(h, cudaMemcpy(aos.data(), h->d.atom_of_slot + W.slot_off, sizeof(int) * nslot, cudaMemcpyDeviceToHost));
+    CU(h, cudaMemcpy(&nsc, h->d.n_sc + walker, sizeof(int), cudaMemcpyDeviceToHost));
+    CU(h, cudaMemcpy(nent.data(), h->d.sc_nent + W.sc_off, sizeof(int) * W.sc_cap, cudaMemcpyDeviceToHost));
+    std::vector<int2> hdr((size_t)W.sc_cap * h->L.ent_cap);
+    std::vector<uint4> msk(2 * hdr.size());
+    CU(h, cudaMemcpy(hdr.data(), h->d.ent_hdr + (size_t)W.sc_off * h->L.ent_cap, sizeof(int2) * hdr.size(),
+                     cudaMemcpyDeviceToHost));
+    CU(h, cudaMemcpy(msk.data(), h->d.ent_mask + 2 * (size_t)W.sc_off * h->L.ent_cap, sizeof(uint4) * msk.size(),
+                     cudaMemcpyDeviceToHost));
+    std::vector<std::pair<long long, int>> out;
+    for (int sl = 0; sl < nsc; ++sl) {
+        for (int e = 0; e < nent[W.sc_off + sl - W.sc_off]; ++e) {
+            const size_t ge = (size_t)sl * h->L.ent_cap + e;
+            const int jbase = hdr[ge].x - W.slot_off;
+            const unsigned imask = (unsigned)hdr[ge].y >> 8;
+            const unsigned m[8] = {msk[2 * ge].x, msk[2 * ge].y, msk[2 * ge].z, msk[2 * ge].w,
+                                   msk[2 * ge + 1].x, msk[2 * ge + 1].y, msk[2 * ge + 1].z, msk[2 * ge + 1].w};
+            for (int ic = 0; ic < NIC; ++ic) {
+                if (!(imask & (1u << ic))) continue;
+                for (int lane = 0; lane < 32; ++lane) {
+                    if (!(m[ic] & (1u << lane))) continue;
+                    const int a = aos[sl * SC + ic * IC + (lane & 7)], b = aos[jbase + (lane >> 3)];
+                    const int i = std::min(a, b), j = std::max(a, b);
+                    out.push_back({(long long)i * S.n_atoms + j, 0});
+                }
+            }
+        }
+    }
+    const int na = S.n_alch;
+    if (na > 0) {
+        std::vector<int> acnt(na), aslot((size_t)na * h->L.alch_cap), aidx(na);
+        CU(h, cudaMemcpy(acnt.data(), h->d.alch_cnt + W.alch_base, sizeof(int) * na, cudaMemcpyDeviceToHost));
+        CU(h, cudaMemcpy(aslot.data(), h->d.alch_slot + (size_t)W.alch_base * h->L.alch_cap,
+                         sizeof(int) * aslot.size(), cudaMemcpyDeviceToHost));
+        CU(h, cudaMemcpy(aidx.data(), h->d.alch_atoms + S.alch_off, sizeof(int) * na, cudaMemcpyDeviceToHost));
+        for (int r = 0; r < na; ++r)
+            for (int k = 0; k < acnt[r]; ++k) {
+                const int b = aos[aslot[(size_t)r * h->L.alch_cap + k] - W.slot_off];
+                const int a = aidx[r];
+                out.push_back({(long long)std::min(a, b) * S.n_atoms + std::max(a, b), 1});
+            }
+    }
+    std::sort(out.begin(), out.end());
+    *count = (int64_t)out.size();
+    for (size_t k = 0; k < out.size() && (int64_t)k < cap; ++k) {
+        if (pairs) {
+            pairs[2 * k] = (int32_t)(out[k].first / S.n_atoms);
+            pairs[2 * k + 1] = (int32_t)(out[k].first % S.n_atoms);
+        }
+        if (kind) kind[k] = (uint8_t)out[k].second;
+    }
+    return LA_OK;
+}
+
+int la_lambda_path(la_handle *h, const double *lam, int n, double b_v, double b_e, double *out, void *stream) {
+    if (!h || !lam || !out || n < 0) return LA_ERR_INVALID_ARG;
+    if ((size_t)n * 5 * sizeof(double) > (size_t)h->io_floats * sizeof(float))
+        return fail(h, LA_ERR_INVALID_ARG, "too many lambda values for the I/O buffer");
+    if (n == 0) return LA_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *dl = (double *)h->io, *dout = dl + n;
+    CU(h, cudaMemcpyAsync(dl, lam, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    launch_lambda_path(dl, n, b_v, b_e, dout, s);
+    CU(h, cudaMemcpyAsync(out, dout, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s));
+    CU(h, cudaStreamSynchronize(s));
+    return LA_OK;
+}
+
+int la_sync(la_handle *h, void *stream, uint32_t *status_bits) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    unsigned bits = 0;
+    int rc = sync_status(h, (cudaStream_t)stream, &bits);
+    if (status_bits) *status_bits = bits;
+    return rc;
+}
+
+int la_stats(la_handle *h, int64_t *out, void *stream) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long c[8];
+    CU(h, cudaMemcpyAsync(c, h->d.counters, sizeof c, cudaMemcpyDeviceToHost, s));
+    std::vector<int> nent(h->L.scs), nsc(h->L.W);
+    CU(h, cudaMemcpyAsync(nent.data(), h->d.sc_nent, sizeof(int) * nent.size(), cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(nsc.data(), h->d.n_sc, sizeof(int) * nsc.size(), cudaMemcpyDeviceToHost, s));
+    CU(h, cudaStreamSynchronize(s));
+    long long ents = 0;
+    for (int w = 0; w < h->L.W; ++w)
+        for (int k = 0; k < nsc[w]; ++k) ents += nent[h->walk[w].sc_off + k];
+    if (out) {
+        out[0] = h->steps;
+        out[1] = (int64_t)c[0];
+        out[2] = h->launches;
+        out[3] = (int64_t)c[1];
+        out[4] = (int64_t)c[2];
+        out[5] = ents;
+        out[6] = -1;  // listed atom pairs: see la_get_pairs
+    }
+    return LA_OK;
+}
+
+int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_out, void *stream) {
+    if (!h || !ms_out || n_steps <= 0) return LA_ERR_INVALID_ARG;
+    int rc = check_posted(h);
+    if (rc != LA_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int W = h->L.W;
+    cudaEvent_t ev[LA_N_KERNELS + 1];
+    for (auto &e : ev) CU(h, cudaEventCreate(&e));
+    double acc[LA_N_KERNELS] = {0};
+    int64_t cnt[LA_N_KERNELS] = {0};
+    const int nbo = h->hv.bo_off[W - 1] + h->hv.n_bo[W - 1];
+    for (int k = 0; k < n_steps; ++k) {
+        cudaEventRecord(ev[0], s);
+        launch_integrate(h->d, h->hv, 0, W, s);
+        cudaEventRecord(ev[1], s);
+        launch_rebuild(h->d, h->hv, 0, W, s);
+        cudaEventRecord(ev[2], s);
+        launch_pairs(h->d, h->hv, 0, W, false, s);
+        cudaEventRecord(ev[3], s);
+        launch_bonded(h->d, h->hv, 0, W, false, s);
+        cudaEventRecord(ev[4], s);
+        launch_walker(h->d, 0, W, false, s);
+        cudaEventRecord(ev[5], s);
+        launch_lambda(h->d, 0, (int)h->stages.size(), false, s);
+        cudaEventRecord(ev[6], s);
+        CU(h, cudaEventSynchronize(ev[6]));
+        for (int q = 0; q < LA_N_KERNELS; ++q) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
+            acc[q] += ms;
+        }
+        cnt[0] += 1;
+        cnt[1] += rebuild_kernel_count(h->hv, 0, W);
+        cnt[2] += 1;
+        cnt[3] += nbo > 0 ? 1 : 0;
+        cnt[4] += 1;
+        cnt[5] += 1;
+    }
+    launch_finish(h->d, h->hv, 0, W, s);
+    h->steps += n_steps;
+    h->launches += n_steps * h->launches_per_step + 1;
+    for (auto &e : ev) cudaEventDestroy(e);
+    for (int q = 0; q < LA_N_KERNELS; ++q) {
+        ms_out[q] = (float)(acc[q] / n_steps);
+        if (launches_out) launches_out[q] = cnt[q];
+    }
+    return sync_status(h, s, nullptr);
+}
+
+const char *la_autotune_report(la_handle *h) { return h ? h->report.c_str() : "no handle"; }
+
+const char *la_last_error(la_handle *h) { return h ? h->err.c_str() : "no handle"; }
+
+int la_destroy(la_handle *h) {
+    if (!h) return LA_OK;
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->status_ev) cudaEventDestroy(h->status_ev);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    delete h;
+    return LA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,32 @@
+// labf_launch.h -- host-side launchers shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "labf_internal.cuh"
+
+#define LA_MAX_WALKERS_PER_LAUNCH 256
+
+namespace labf {
+
+// Host copies of the per-walker offsets the launchers size grids with.
+struct HostView {
+    int n_walkers = 0, n_sm = 0, pair_blocks = 0;
+    const int *slot_off = nullptr, *slot_cap = nullptr, *sc_cap = nullptr, *n_cols = nullptr;
+    const int *alch_base = nullptr, *n_alch = nullptr, *item_cap = nullptr;
+    const int *bo_off = nullptr, *n_bo = nullptr;
+};
+
+void launch_integrate(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
+void launch_finish(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
+void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
+int rebuild_kernel_count(const HostView &hv, int w0, int w1);
+void launch_pairs(const Dev &d, const HostView &hv, int w0, int w1, bool energy, cudaStream_t s);
+void launch_bonded(const Dev &d, const HostView &hv, int w0, int w1, bool energy, cudaStream_t s);
+void launch_walker(const Dev &d, int w0, int w1, bool energy, cudaStream_t s);
+void launch_lambda(const Dev &d, int s0, int s1, bool prime, cudaStream_t s);
+void launch_state_io(const Dev &d, int w, int n, float *x, float *v, bool to_slots, cudaStream_t s);
+void launch_forces_out(const Dev &d, int w, int n, float *out, cudaStream_t s);
+void launch_lambda_path(const double *lam, int n, double bv, double be, double *out, cudaStream_t s);
+
+}  // namespace labf

@@ -1,0 +1,374 @@
+"""Python binding of liblabf (include/labf.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module converts
+numpy/torch objects into the C ABI's pointers and back.  PyTorch provides
+the device arena (one uint8 tensor) and the stream.  If the compiled
+library is missing the import of :func:`load` raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+LA_OK = 0
+LA_WARN_EMPTY_BIN = 1
+LA_N_TERMS = 7
+LA_N_STATS = 7
+LA_N_KERNELS = 6
+LA_EF_REBUILD = 0x1
+LA_EF_COUNT_PAIRS = 0x2
+TERM_NAMES = ("lj", "rf", "sc_lj", "sc_rf", "bond", "angle", "restraint")
+KERNEL_NAMES = ("integrate", "rebuild", "pairs", "bonded", "walker", "lambda")
+ERRORS = {-1: "INVALID_ARG", -2: "BOX_TOO_SMALL", -3: "CUDA", -4: "UNSUPPORTED", -5: "ARENA_TOO_SMALL",
+          -6: "LIST_OVERFLOW", -7: "NONFINITE", -8: "FIXED_OVERFLOW", -9: "STATE"}
+
+EXPORTED = ("la_query_sizes", "la_create_system", "la_step_walkers", "la_step_walkers_plain",
+            "la_read_abf", "la_energy_forces", "la_get_state", "la_set_state", "la_set_alch_params",
+            "la_read_theta", "la_get_pairs", "la_lambda_path", "la_sync", "la_stats",
+            "la_time_kernels", "la_autotune_report", "la_last_error", "la_destroy")
+
+
+class LabfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"labf error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class la_system_desc(C.Structure):
+    _fields_ = [
+        ("n_atoms", C.c_int32), ("box", C.c_double),
+        ("mass", C.c_void_p), ("charge", C.c_void_p), ("sigma", C.c_void_p), ("epsilon", C.c_void_p),
+        ("alch", C.c_void_p), ("excl_group", C.c_void_p), ("excl_extra", C.c_void_p),
+        ("n_bonds", C.c_int32), ("bond_ij", C.c_void_p), ("bond_r0", C.c_void_p), ("bond_k", C.c_void_p),
+        ("n_angles", C.c_int32), ("angle_ijk", C.c_void_p), ("angle_t0", C.c_void_p),
+        ("angle_k", C.c_void_p),
+        ("n_posres", C.c_int32), ("posres_idx", C.c_void_p), ("posres_x0", C.c_void_p),
+        ("posres_k", C.c_double),
+        ("n_fb_a", C.c_int32), ("fb_a", C.c_void_p), ("n_fb_b", C.c_int32), ("fb_b", C.c_void_p),
+        ("fb_d0", C.c_double), ("fb_k", C.c_double),
+        ("n_lh", C.c_int32), ("lh_idx", C.c_void_p), ("lh_x0", C.c_void_p),
+        ("lh_k0", C.c_double), ("lh_k1", C.c_double), ("lh_dims", C.c_int32),
+        ("r_cut", C.c_double), ("eps_rf", C.c_double), ("coul", C.c_double),
+        ("b_v", C.c_double), ("b_e", C.c_double), ("sc_alpha", C.c_double),
+        ("sc_n", C.c_int32), ("sc_m", C.c_int32),
+        ("kT", C.c_double), ("dt", C.c_double), ("gamma", C.c_double), ("m_lambda", C.c_double),
+        ("gamma_lambda", C.c_double), ("skin", C.c_double), ("n_full", C.c_double),
+        ("shared_freq", C.c_int32), ("seed", C.c_uint32),
+        ("lambda_dynamics", C.c_int32), ("abf_on", C.c_int32), ("theta_stats", C.c_int32),
+        ("n_stages", C.c_int32),
+        ("stage_lo", C.c_void_p), ("stage_hi", C.c_void_p), ("stage_bins", C.c_void_p),
+        ("stage_walkers", C.c_void_p),
+        ("x0", C.c_void_p), ("v0", C.c_void_p), ("lam0", C.c_void_p), ("plam0", C.c_void_p),
+    ]
+
+
+class la_options(C.Structure):
+    _fields_ = [("graph_steps", C.c_int32), ("autotune", C.c_int32),
+                ("list_capacity_factor", C.c_double), ("pair_warps", C.c_int32),
+                ("pair_ctas_per_sm", C.c_int32), ("chunk_entries", C.c_int32)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load liblabf.so.  Raises if it is missing (no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"liblabf.so not built at {path}: run __graft_entry__.build()")
+        _build.build()
+    lib = C.CDLL(path)
+    P, I, D, S = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    H = C.c_void_p
+    lib.la_query_sizes.argtypes = [P, I, P, C.POINTER(S)]
+    lib.la_create_system.argtypes = [P, I, P, P, S, P, C.POINTER(H)]
+    lib.la_step_walkers.argtypes = [H, C.c_int64, P]
+    lib.la_step_walkers_plain.argtypes = [H, C.c_int64, P]
+    lib.la_read_abf.argtypes = [H, I, I, P, P, P, P, P, P, P, P]
+    lib.la_energy_forces.argtypes = [H, I, C.c_uint32, P, P, P, P, P, P]
+    lib.la_get_state.argtypes = [H, I, P, P, P, P, P, P]
+    lib.la_set_state.argtypes = [H, I, P, P, P, P, P]
+    lib.la_set_alch_params.argtypes = [H, I, P, P]
+    lib.la_read_theta.argtypes = [H, I, I, P, P, P, P]
+    lib.la_get_pairs.argtypes = [H, I, P, P, C.c_int64, P, P]
+    lib.la_lambda_path.argtypes = [H, P, I, D, D, P, P]
+    lib.la_sync.argtypes = [H, P, P]
+    lib.la_stats.argtypes = [H, P, P]
+    lib.la_time_kernels.argtypes = [H, I, P, P, P]
+    lib.la_autotune_report.argtypes = [H]
+    lib.la_autotune_report.restype = C.c_char_p
+    lib.la_last_error.argtypes = [H]
+    lib.la_last_error.restype = C.c_char_p
+    lib.la_destroy.argtypes = [H]
+    for name in EXPORTED:
+        if name not in ("la_autotune_report", "la_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class _Keep:
+    """Holds numpy arrays referenced by a descriptor until create returns."""
+
+    def __init__(self):
+        self.items = []
+
+    def arr(self, a, dt, shape=None):
+        a = np.ascontiguousarray(a, dtype=dt)
+        if shape is not None:
+            a = a.reshape(shape)
+        self.items.append(a)
+        return _p(a) if a.size else None
+
+
+def make_desc(spec, run, state, keep: _Keep) -> la_system_desc:
+    """Marshal a SystemSpec / RunSpec / WalkerState into la_system_desc."""
+    d = la_system_desc()
+    k = keep
+    d.n_atoms = spec.n
+    d.box = float(spec.box)
+    d.mass = k.arr(spec.mass, np.float64)
+    d.charge = k.arr(spec.charge, np.float64)
+    d.sigma = k.arr(spec.sigma, np.float64)
+    d.epsilon = k.arr(spec.epsilon, np.float64)
+    d.alch = k.arr(spec.alch, np.uint8)
+    d.excl_group = k.arr(spec.excl_group, np.int32)
+    d.excl_extra = k.arr(spec.excl_extra, np.int32)
+    d.n_bonds = len(spec.bond_r0)
+    d.bond_ij = k.arr(spec.bond_ij, np.int32)
+    d.bond_r0 = k.arr(spec.bond_r0, np.float64)
+    d.bond_k = k.arr(spec.bond_k, np.float64)
+    d.n_angles = len(spec.angle_t0)
+    d.angle_ijk = k.arr(spec.angle_ijk, np.int32)
+    d.angle_t0 = k.arr(spec.angle_t0, np.float64)
+    d.angle_k = k.arr(spec.angle_k, np.float64)
+    d.n_posres = len(spec.posres_idx)
+    d.posres_idx = k.arr(spec.posres_idx, np.int32)
+    d.posres_x0 = k.arr(spec.posres_x0, np.float64)
+    d.posres_k = float(spec.posres_k)
+    d.n_fb_a, d.fb_a = len(spec.fb_a), k.arr(spec.fb_a, np.int32)
+    d.n_fb_b, d.fb_b = len(spec.fb_b), k.arr(spec.fb_b, np.int32)
+    d.fb_d0, d.fb_k = float(spec.fb_d0), float(spec.fb_k)
+    d.n_lh, d.lh_idx = len(spec.lh_idx), k.arr(spec.lh_idx, np.int32)
+    d.lh_x0 = k.arr(spec.lh_x0, np.float64)
+    d.lh_k0, d.lh_k1, d.lh_dims = float(spec.lh_k0), float(spec.lh_k1), int(spec.lh_dims)
+    d.r_cut, d.eps_rf, d.coul = float(spec.r_cut), float(spec.eps_rf), float(spec.coul)
+    d.b_v, d.b_e, d.sc_alpha = float(spec.b_v), float(spec.b_e), float(spec.sc_alpha)
+    d.sc_n, d.sc_m = int(spec.sc_n), int(spec.sc_m)
+    d.kT, d.dt, d.gamma = float(run.kT), float(run.dt), float(run.gamma)
+    d.m_lambda, d.gamma_lambda = float(run.m_lambda), float(run.gamma_lambda)
+    d.skin, d.n_full = float(run.skin), float(run.n_full)
+    d.shared_freq, d.seed = int(run.shared_freq), int(run.seed) & 0xFFFFFFFF
+    d.lambda_dynamics, d.abf_on = int(run.lambda_dynamics), int(run.abf_on)
+    d.theta_stats = int(run.theta_stats)
+    d.n_stages = len(run.stages)
+    d.stage_lo = k.arr([s.lo for s in run.stages], np.float64)
+    d.stage_hi = k.arr([s.hi for s in run.stages], np.float64)
+    d.stage_bins = k.arr([s.n_bins for s in run.stages], np.int32)
+    d.stage_walkers = k.arr([s.n_walkers for s in run.stages], np.int32)
+    d.x0 = k.arr(state.x, np.float32)
+    d.v0 = k.arr(state.v, np.float32)
+    d.lam0 = k.arr(state.lam, np.float64)
+    d.plam0 = k.arr(state.plam, np.float64)
+    return d
+
+
+@dataclass
+class SystemInput:
+    spec: object
+    run: object
+    state: object
+
+
+class Engine:
+    """An engine instance over one or more systems (their walkers batched).
+
+    The device arena is one torch uint8 tensor; all device work goes on the
+    current torch stream of the arena's device unless a stream is given.
+    """
+
+    def __init__(self, systems: Sequence[SystemInput], options: Optional[dict] = None,
+                 device: int = 0):
+        import torch
+
+        self.torch = torch
+        self.lib = load()
+        self.systems = list(systems)
+        keep = _Keep()
+        descs = (la_system_desc * len(self.systems))()
+        for i, s in enumerate(self.systems):
+            descs[i] = make_desc(s.spec, s.run, s.state, keep)
+        opt = la_options()
+        for k, v in (options or {}).items():
+            setattr(opt, k, v)
+        self._opt = opt
+        nbytes = C.c_size_t(0)
+        self._check(self.lib.la_query_sizes(C.cast(descs, C.c_void_p), len(descs), C.byref(opt),
+                                            C.byref(nbytes)), None)
+        self.device = torch.device("cuda", device)
+        self.arena = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+        self.handle = C.c_void_p()
+        rc = self.lib.la_create_system(C.cast(descs, C.c_void_p), len(descs), C.byref(opt),
+                                       C.c_void_p(self.arena.data_ptr()), nbytes, self._stream(),
+                                       C.byref(self.handle))
+        self._check(rc)
+        del keep
+        self.walker_sys, self.walker_local = [], []
+        for si, s in enumerate(self.systems):
+            for wl in range(s.run.n_walkers):
+                self.walker_sys.append(si)
+                self.walker_local.append(wl)
+        self.n_walkers = len(self.walker_sys)
+
+    # -- plumbing -------------------------------------------------------
+    def _stream(self, stream=None):
+        if stream is None:
+            stream = self.torch.cuda.current_stream(self.device)
+        return C.c_void_p(stream.cuda_stream)
+
+    def _check(self, rc, handle="self"):
+        if rc < 0:
+            h = self.handle if handle == "self" else None
+            msg = self.lib.la_last_error(h).decode() if h else ""
+            raise LabfError(rc, msg)
+        return rc
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.la_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- stepping ---------------------------------------------------------
+    def step(self, n_steps: int, stream=None):
+        self._check(self.lib.la_step_walkers(self.handle, int(n_steps), self._stream(stream)))
+
+    def step_plain(self, n_steps: int, stream=None):
+        self._check(self.lib.la_step_walkers_plain(self.handle, int(n_steps), self._stream(stream)))
+
+    def sync(self, stream=None) -> int:
+        bits = C.c_uint32(0)
+        self._check(self.lib.la_sync(self.handle, self._stream(stream), C.byref(bits)))
+        return int(bits.value)
+
+    # -- read-outs --------------------------------------------------------
+    def read_abf(self, sys: int = 0, stage: int = 0, stream=None) -> dict:
+        nb = self.systems[sys].run.stages[stage].n_bins
+        s1, s2, A = np.zeros(nb), np.zeros(nb), np.zeros(nb + 1)
+        cnt = np.zeros(nb, np.int64)
+        grad = np.zeros(nb)
+        dA, se = C.c_double(0), C.c_double(0)
+        rc = self.lib.la_read_abf(self.handle, sys, stage, _p(s1), _p(s2), _p(cnt), _p(grad), _p(A),
+                                  C.byref(dA), C.byref(se), self._stream(stream))
+        self._check(rc)
+        return dict(sum=s1, sumsq=s2, count=cnt, grad=grad, A=A, dA=dA.value, dA_se=se.value,
+                    empty_bin=rc == LA_WARN_EMPTY_BIN)
+
+    def energy_forces(self, walker: int, rebuild: bool = False, count_pairs: bool = False,
+                      forces: bool = True, stream=None) -> dict:
+        si = self.walker_sys[walker]
+        spec = self.systems[si].spec
+        P = 3 * spec.n_alch + 1
+        terms = np.zeros(LA_N_TERMS)
+        dudl = C.c_double(0)
+        dth, d2 = np.zeros(P), np.zeros(P)
+        f = self.torch.zeros((spec.n, 3), dtype=self.torch.float32, device=self.device) if forces else None
+        flags = (LA_EF_REBUILD if rebuild else 0) | (LA_EF_COUNT_PAIRS if count_pairs else 0)
+        self._check(self.lib.la_energy_forces(self.handle, walker, flags, _p(terms),
+                                              C.c_void_p(f.data_ptr()) if f is not None else None,
+                                              C.byref(dudl), _p(dth), _p(d2), self._stream(stream)))
+        out = dict(terms=terms, U=float(terms.sum()), dUdl=dudl.value, dth=dth, d2th=d2, F=f)
+        if count_pairs:
+            st = self.stats(stream)
+            out["pairs_normal"], out["pairs_alch"] = int(st[3]), int(st[4])
+        return out
+
+    def get_state(self, walker: int, stream=None) -> dict:
+        n = self.systems[self.walker_sys[walker]].spec.n
+        x, v = np.zeros((n, 3), np.float32), np.zeros((n, 3), np.float32)
+        lam, plam, step = C.c_double(0), C.c_double(0), C.c_uint64(0)
+        self._check(self.lib.la_get_state(self.handle, walker, _p(x), _p(v), C.byref(lam), C.byref(plam),
+                                          C.byref(step), self._stream(stream)))
+        return dict(x=x, v=v, lam=lam.value, plam=plam.value, step=step.value)
+
+    def set_state(self, walker: int, x=None, v=None, lam=None, plam=None, stream=None):
+        xa = None if x is None else np.ascontiguousarray(x, np.float32)
+        va = None if v is None else np.ascontiguousarray(v, np.float32)
+        la = None if lam is None else C.byref(C.c_double(float(lam)))
+        pa = None if plam is None else C.byref(C.c_double(float(plam)))
+        self._check(self.lib.la_set_state(self.handle, walker, _p(xa), _p(va), la, pa, self._stream(stream)))
+
+    def set_alch_params(self, sys: int, theta: np.ndarray, stream=None):
+        t = np.ascontiguousarray(theta, np.float64)
+        self._check(self.lib.la_set_alch_params(self.handle, sys, _p(t), self._stream(stream)))
+
+    def read_theta(self, sys: int = 0, stage: int = 0, stream=None) -> dict:
+        spec = self.systems[sys].spec
+        nb = self.systems[sys].run.stages[stage].n_bins
+        P = 3 * spec.n_alch + 1
+        a, b, c = np.zeros((nb, P)), np.zeros((nb, P)), np.zeros((nb, P))
+        self._check(self.lib.la_read_theta(self.handle, sys, stage, _p(a), _p(b), _p(c), self._stream(stream)))
+        return dict(sum_d2=a, sum_d=b, sum_sd=c)
+
+    def get_pairs(self, walker: int, stream=None) -> Tuple[np.ndarray, np.ndarray]:
+        cnt = C.c_int64(0)
+        self._check(self.lib.la_get_pairs(self.handle, walker, None, None, 0, C.byref(cnt), self._stream(stream)))
+        n = int(cnt.value)
+        pairs = np.zeros((max(n, 1), 2), np.int32)
+        kind = np.zeros(max(n, 1), np.uint8)
+        self._check(self.lib.la_get_pairs(self.handle, walker, _p(pairs), _p(kind), n, C.byref(cnt),
+                                          self._stream(stream)))
+        return pairs[:n], kind[:n]
+
+    def lambda_path(self, lam: np.ndarray, b_v: float, b_e: float, stream=None) -> np.ndarray:
+        lam = np.ascontiguousarray(lam, np.float64)
+        out = np.zeros((lam.size, 4))
+        self._check(self.lib.la_lambda_path(self.handle, _p(lam), lam.size, float(b_v), float(b_e), _p(out),
+                                            self._stream(stream)))
+        return out
+
+    def stats(self, stream=None) -> np.ndarray:
+        out = np.zeros(LA_N_STATS, np.int64)
+        self._check(self.lib.la_stats(self.handle, _p(out), self._stream(stream)))
+        return out
+
+    def time_kernels(self, n_steps: int, stream=None) -> dict:
+        ms = np.zeros(LA_N_KERNELS, np.float32)
+        cnt = np.zeros(LA_N_KERNELS, np.int64)
+        self._check(self.lib.la_time_kernels(self.handle, int(n_steps), _p(ms), _p(cnt), self._stream(stream)))
+        return {k: (float(m), int(c)) for k, m, c in zip(KERNEL_NAMES, ms, cnt)}
+
+    def autotune_report(self) -> str:
+        return self.lib.la_autotune_report(self.handle).decode()
+
+
+def engine_for(spec, run, state=None, options=None) -> Engine:
+    """One-system convenience constructor."""
+    from . import synth
+
+    st = state if state is not None else synth.initial_state(spec, run)
+    return Engine([SystemInput(spec, run, st)], options)

@@ -1,0 +1,83 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol
+that include/labf.h declares; descriptor layouts agree with the header."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from paper_2307_08006_gb300 import build as engine_build
+from paper_2307_08006_gb300 import labf, synth
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "labf.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(la_\w+)\s*\(", src, re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = engine_build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (la_\w+)", out))
+    declared = _declared()
+    assert declared, "no declarations parsed"
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    assert set(declared) == set(labf.EXPORTED)
+
+
+def test_library_loads_without_gpu():
+    lib = labf.load(build_if_missing=True)
+    for name in labf.EXPORTED:
+        assert hasattr(lib, name)
+
+
+def test_descriptor_layout_matches_header(tmp_path):
+    prog = tmp_path / "sz.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "labf.h"\n'
+                    'int main(){printf("%zu %zu %zu %zu %zu\\n", sizeof(la_system_desc),'
+                    ' offsetof(la_system_desc, kT), offsetof(la_system_desc, plam0),'
+                    ' offsetof(la_system_desc, seed), sizeof(la_options));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    D = labf.la_system_desc
+    assert got == [C.sizeof(D), D.kT.offset, D.plam0.offset, D.seed.offset, C.sizeof(labf.la_options)]
+
+
+def _query(spec, run, state=None, opt=None):
+    lib = labf.load(build_if_missing=True)
+    keep = labf._Keep()
+    st = state if state is not None else synth.initial_state(spec, run)
+    d = labf.make_desc(spec, run, st, keep)
+    n = C.c_size_t(0)
+    rc = lib.la_query_sizes(C.byref(d), 1, opt, C.byref(n))
+    return rc, n.value
+
+
+def test_query_sizes_host_only():
+    rc, n = _query(synth.lj_fluid(), synth.lj_fluid_run())
+    assert rc == 0 and n > 0 and n % 256 == 0
+    rc2, n2 = _query(synth.water_box(), synth.water_run())
+    assert rc2 == 0 and n2 > n
+
+
+def test_query_rejects_bad_input():
+    sp = synth.water_box(64, 4, box=1.25, r_cut=0.5)
+    run = synth.water_run(walkers_per_stage=1)
+    assert _query(sp, run)[0] == 0
+    # box smaller than twice the list radius
+    small = synth.with_changes(sp, r_cut=0.6)
+    assert _query(small, run)[0] == -2
+    # non-positive mass, out-of-range bond index, empty stage list
+    bad = synth.with_changes(sp, mass=np.where(np.arange(sp.n) == 3, 0.0, sp.mass))
+    assert _query(bad, run)[0] == -1
+    bi = sp.bond_ij.copy()
+    bi[0, 1] = sp.n
+    assert _query(synth.with_changes(sp, bond_ij=bi), run)[0] == -1
+    run0 = synth.water_run(walkers_per_stage=1)
+    run0.stages = []
+    assert _query(sp, run0)[0] == -1

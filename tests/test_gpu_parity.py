@@ -1,0 +1,186 @@
+"""GPU parity: the CUDA engine (through the C ABI) against the FP64 oracle on
+identical seeded inputs.
+
+Bars: pair sets bit-exact (integer definition); forces within 1e-5 relative
+RMS; dU/dlambda and energy terms within 1e-5 relative to their scale;
+lambda path exact; short trajectories (same Philox streams) within FP32
+rounding growth; batched and one-walker-per-launch forms bit-identical;
+repeated runs bit-identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import read_golden
+from paper_2307_08006_gb300 import labf, synth
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-5
+
+
+def rel_rms(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
+
+
+def small_water(n_w=100, n_s=6, box=1.5, rc=0.6, seed=31, jitter=0.0):
+    sp = synth.water_box(n_w, n_s, seed=seed, box=box, r_cut=rc)
+    if jitter:
+        rng = np.random.default_rng(seed)
+        sp.x = ((sp.x + rng.normal(0, jitter, sp.x.shape)) % box).astype(np.float32)
+    return sp
+
+
+def make_engine(spec, run, lam0=None, state=None, **opt):
+    st = state if state is not None else synth.initial_state(spec, run, lam0=lam0)
+    return labf.engine_for(spec, run, st, options=opt or None), st
+
+
+def check_forces(eng, spec, st, walker, lam=None, tol=FORCE_TOL):
+    osys = oracle.OracleSystem(spec)
+    g = eng.energy_forces(walker)
+    ref = oracle.energy_forces(osys, st.x[walker].astype(np.float64), st.lam[walker] if lam is None else lam)
+    f = g["F"].cpu().numpy().astype(np.float64)
+    assert rel_rms(f, ref["F"]) < tol
+    scale = max(1.0, float(np.abs(ref["terms"]).max()))
+    np.testing.assert_allclose(g["terms"], ref["terms"], rtol=tol, atol=tol * scale)
+    dscale = max(1.0, abs(ref["dl"][0]) + abs(ref["dl"][1]) + abs(ref["dl"][2]))
+    assert abs(g["dUdl"] - ref["dUdl"]) <= tol * dscale
+    return g, ref
+
+
+# ---------------------------------------------------------------------------
+def test_lambda_path_device_matches_table_and_oracle():
+    sp = small_water()
+    eng, _ = make_engine(sp, synth.water_run(walkers_per_stage=1))
+    rows = read_golden("lambda_schedule_tableS1.txt")
+    lam = np.array([float(r[0]) for r in rows])
+    out = eng.lambda_path(lam, 0.5, 0.5)
+    np.testing.assert_allclose(out[:, 0], [float(r[2]) for r in rows], atol=1e-12)
+    np.testing.assert_allclose(out[:, 1], [float(r[1]) for r in rows], atol=1e-12)
+    rng = np.random.default_rng(1)
+    for bv, be in ((0.5, 0.5), (1.0, 0.0), (0.7, 0.3)):
+        lam = np.concatenate([rng.uniform(0, 1, 500), [0.0, 1.0, bv, be]])
+        out = eng.lambda_path(lam, bv, be)
+        ref = np.array([oracle.lambda_path(v, bv, be) for v in lam])
+        assert np.array_equal(out, ref)
+
+
+@pytest.mark.parametrize("case", ["water_small", "water_ragged", "water_min_box", "lj_fluid"])
+def test_pair_set_bit_exact(case):
+    if case == "water_small":
+        sp, run = small_water(jitter=0.02), synth.water_run(walkers_per_stage=1)
+    elif case == "water_ragged":
+        sp, run = small_water(n_w=137, n_s=5, box=1.7, seed=5, jitter=0.03), synth.water_run(walkers_per_stage=1)
+    elif case == "water_min_box":
+        # box just above 2 r_list: several periodic images per cluster pair
+        sp = small_water(n_w=64, n_s=4, box=1.25, rc=0.52, seed=7, jitter=0.02)
+        run = synth.water_run(walkers_per_stage=1, skin=0.1)
+    else:
+        sp, run = synth.lj_fluid(), synth.lj_fluid_run(n_walkers=2)
+    eng, st = make_engine(sp, run)
+    osys = oracle.OracleSystem(sp)
+    for w in range(run.n_walkers):
+        pairs, kind = eng.get_pairs(w)
+        opairs, okind = oracle.pair_set(osys, st.x[w], sp.r_cut + run.skin)
+        assert len(pairs) == len(opairs)
+        assert np.array_equal(pairs, opairs)
+        assert np.array_equal(kind, okind)
+
+
+@pytest.mark.parametrize("lam0", [[0.0, 0.13, 0.37, 0.5], [0.5, 0.62, 0.91, 1.0]])
+def test_forces_energies_dudl_water(lam0):
+    sp = small_water(jitter=0.01)
+    run = synth.water_run(walkers_per_stage=2, n_bins=20)
+    eng, st = make_engine(sp, run, lam0=lam0)
+    for w in range(run.n_walkers):
+        check_forces(eng, sp, st, w)
+
+
+def test_forces_lj_fluid():
+    sp = synth.lj_fluid()
+    run = synth.lj_fluid_run(n_walkers=4)
+    eng, st = make_engine(sp, run, lam0=[0.0, 0.3, 0.75, 1.0])
+    for w in range(4):
+        check_forces(eng, sp, st, w)
+
+
+def test_theta_derivatives():
+    sp = small_water(jitter=0.01)
+    run = synth.water_run(walkers_per_stage=2, n_bins=20)
+    eng, st = make_engine(sp, run, lam0=[0.15, 0.4, 0.6, 0.85])
+    osys = oracle.OracleSystem(sp)
+    for w in range(4):
+        g = eng.energy_forces(w)
+        ref = oracle.energy_forces(osys, st.x[w].astype(np.float64), st.lam[w])
+        for key in ("dth", "d2th"):
+            scale = max(1.0, float(np.abs(ref[key]).max()))
+            np.testing.assert_allclose(g[key], ref[key], rtol=1e-4, atol=1e-5 * scale)
+
+
+def test_short_trajectory_matches_oracle():
+    sp = small_water(jitter=0.01)
+    run = synth.water_run(walkers_per_stage=2, n_bins=20)
+    st = synth.initial_state(sp, run, lam0=[0.1, 0.3, 0.6, 0.8])
+    eng, _ = make_engine(sp, run, state=st)
+    sim = oracle.Simulation(sp, run, st)
+    for chunk in (1, 2, 3):
+        eng.step(chunk)
+        sim.run(chunk)
+        for w in range(run.n_walkers):
+            s = eng.get_state(w)
+            d = s["x"] - sim.a["x"][w]
+            d -= sp.box * np.round(d / sp.box)
+            assert np.abs(d).max() < 2e-5
+            assert np.abs(s["v"] - sim.a["v"][w]).max() < 2e-3 * np.abs(sim.a["v"][w]).max()
+            assert s["lam"] == pytest.approx(sim.a["lam"][w], abs=1e-7)
+    for stage in range(2):
+        a = eng.read_abf(0, stage)
+        s, _, c = sim.stage_bins(stage)
+        assert np.array_equal(a["count"], c)
+        np.testing.assert_allclose(a["sum"], s, rtol=1e-4, atol=1e-3 * np.abs(s).max())
+
+
+def test_batched_and_plain_forms_are_bit_identical():
+    sp = small_water(jitter=0.01)
+    run = synth.water_run(walkers_per_stage=2, n_bins=20)
+    st = synth.initial_state(sp, run, lam0=[0.1, 0.3, 0.6, 0.8])
+    e1, _ = make_engine(sp, run, state=st, graph_steps=4)
+    e2, _ = make_engine(sp, run, state=st, graph_steps=4)
+    e1.step(23)
+    e2.step_plain(23)
+    for w in range(run.n_walkers):
+        a, b = e1.get_state(w), e2.get_state(w)
+        assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v"], b["v"])
+        assert a["lam"] == b["lam"] and a["plam"] == b["plam"] and a["step"] == b["step"] == 23
+    for stage in range(2):
+        ra, rb = e1.read_abf(0, stage), e2.read_abf(0, stage)
+        assert np.array_equal(ra["sum"], rb["sum"]) and np.array_equal(ra["count"], rb["count"])
+
+
+def test_repeat_runs_bit_identical():
+    sp = small_water(jitter=0.01)
+    run = synth.water_run(walkers_per_stage=2, n_bins=20)
+    st = synth.initial_state(sp, run, lam0=[0.1, 0.3, 0.6, 0.8])
+    outs = []
+    for _ in range(2):
+        e, _ = make_engine(sp, run, state=st)
+        e.step(40)
+        outs.append([e.get_state(w) for w in range(4)] + [e.energy_forces(0)["F"].cpu().numpy()])
+    for a, b in zip(outs[0][:4], outs[1][:4]):
+        assert np.array_equal(a["x"], b["x"]) and a["lam"] == b["lam"]
+    assert np.array_equal(outs[0][4], outs[1][4])
+
+
+def test_single_atom_system_and_rebuilds():
+    sp = synth.harmonic_well(dims=3)
+    run = synth.harmonic_run(n_walkers=4)
+    eng, st = make_engine(sp, run)
+    eng.step(200)
+    eng.sync()
+    sim = oracle.Simulation(sp, run, st)
+    sim.run(200)
+    for w in range(4):
+        s = eng.get_state(w)
+        assert np.abs(s["x"] - sim.a["x"][w]).max() < 1e-3
+        assert s["lam"] == pytest.approx(sim.a["lam"][w], abs=1e-4)
