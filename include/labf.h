@@ -297,6 +297,67 @@ const char *la_last_error(la_handle *h);
 /* la_destroy: free host metadata and CUDA graphs; never touches the arena. */
 int la_destroy(la_handle *h);
 
+/*
+ * la_alch_pairs_static: the alchemical part of the pair pass for one
+ * configuration, for callers that cannot allocate device memory.  (The
+ * paper has no counterpart; this is a deployment aid.)
+ *
+ * Who needs it: code that runs as a plugin inside another program that owns
+ * the GPU's memory (for example an MD engine that hands a force routine its
+ * own buffers and forbids further allocations), and code that must keep a
+ * fixed device footprint declared up front.  Such callers cannot create an
+ * engine (la_create_system needs a caller-allocated arena), so this entry
+ * point needs no handle and calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *
+ * It evaluates, for every alchemical atom a and every non-alchemical atom b
+ * of another exclusion group within r_cut (minimum image in a cubic box of
+ * edge `box`), the soft-core LJ lambda_v^sc_n 4 eps (s^-2 - s^-1),
+ * s = sc_alpha (1 - lambda_v)^sc_m + (r/sigma)^6 (Lorentz-Berthelot mixing),
+ * plus lambda_e times the reaction-field term coul q_a q_b (1/r + k_rf r^2 -
+ * c_rf), with (lambda_v, lambda_e) from lam by the b_v / b_e path.  Pairs
+ * are scanned directly (no neighbour list).  Only excl_group exclusions
+ * apply (no per-atom extra exclusion lists).
+ *
+ * Inputs (device memory, caller-owned): x [n_atoms][3] float32, q, sigma,
+ * epsilon [n_atoms] float32, alch [n_atoms] uint8 (1 = alchemical),
+ * excl_group [n_atoms] int32 (-1 = none), alch_idx [n_alch] int32 (the
+ * indices of the alchemical atoms, ascending).
+ * Outputs (device memory, caller-owned, overwritten): forces [n_atoms][3]
+ * float32 = minus the gradient of these pair terms; out [5] double =
+ * {dU/dlambda, dU/dlambda_v, dU/dlambda_e, soft-core LJ energy,
+ * lambda_e * RF energy}.
+ *
+ * Scratch: one file-scope static device array of 3 * LA_STATIC_MAX_ATOMS
+ * 64-bit force accumulators plus 4 * LA_STATIC_MAX_ALCH doubles (about
+ * 3.2 MB), held by every GPU that loads the library until the process
+ * exits.  Each call clears the part it uses before using it.  All calls on
+ * a device share that one array, so calls whose GPU work overlaps (on
+ * different streams, or from different threads) race and corrupt each
+ * other's results; serialise them.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (with that device current); make that first call before any stream
+ * capture begins.
+ *
+ * Errors: LA_ERR_INVALID_ARG for NULL pointers, non-positive sizes or box,
+ * n_atoms > LA_STATIC_MAX_ATOMS or n_alch > LA_STATIC_MAX_ALCH (the message
+ * of la_static_last_error names the limit); LA_ERR_CUDA if the set-up or a
+ * launch fails.  Asynchronous on `stream`.
+ */
+#define LA_STATIC_MAX_ATOMS 131072
+#define LA_STATIC_MAX_ALCH 1024
+int la_alch_pairs_static(int n_atoms, const float *x, const float *q, const float *sigma,
+                         const float *epsilon, const uint8_t *alch, const int32_t *excl_group,
+                         int n_alch, const int32_t *alch_idx, double box, double r_cut,
+                         double eps_rf, double coul, double lam, double b_v, double b_e,
+                         double sc_alpha, int sc_n, int sc_m, float *forces, double *out,
+                         void *stream);
+
+/* la_static_last_error: message of the last failing la_alch_pairs_static call
+ * on this thread. */
+const char *la_static_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "BOX_TOO_SMALL", -3: "CUDA", -4: "UNSUPPORTED",
 EXPORTED = ("la_query_sizes", "la_create_system", "la_step_walkers", "la_step_walkers_plain",
             "la_read_abf", "la_energy_forces", "la_get_state", "la_set_state", "la_set_alch_params",
             "la_read_theta", "la_get_pairs", "la_lambda_path", "la_sync", "la_stats",
-            "la_time_kernels", "la_autotune_report", "la_last_error", "la_destroy")
+            "la_time_kernels", "la_autotune_report", "la_last_error", "la_destroy",
+            "la_alch_pairs_static", "la_static_last_error")
 
 
 class LabfError(RuntimeError):
@@ -115,8 +116,11 @@ def load(build_if_missing: bool = False):
     lib.la_last_error.argtypes = [H]
     lib.la_last_error.restype = C.c_char_p
     lib.la_destroy.argtypes = [H]
+    lib.la_alch_pairs_static.argtypes = [I, P, P, P, P, P, P, I, P, D, D, D, D, D, D, D, D, I, I, P, P, P]
+    lib.la_static_last_error.argtypes = []
+    lib.la_static_last_error.restype = C.c_char_p
     for name in EXPORTED:
-        if name not in ("la_autotune_report", "la_last_error"):
+        if name not in ("la_autotune_report", "la_last_error", "la_static_last_error"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -372,3 +376,27 @@ def engine_for(spec, run, state=None, options=None) -> Engine:
 
     st = state if state is not None else synth.initial_state(spec, run)
     return Engine([SystemInput(spec, run, st)], options)
+
+
+def alch_pairs_static(x, q, sigma, epsilon, alch, excl_group, alch_idx, box, r_cut, eps_rf, coul, lam,
+                      b_v, b_e, sc_alpha=0.5, sc_n=1, sc_m=1, forces=None, out=None, stream=None):
+    """Marshal torch CUDA tensors into la_alch_pairs_static (no allocation
+    in the library; `forces` and `out` may be passed pre-allocated)."""
+    import torch
+
+    lib = load()
+    n = int(x.shape[0])
+    if forces is None:
+        forces = torch.empty((n, 3), dtype=torch.float32, device=x.device)
+    if out is None:
+        out = torch.empty(5, dtype=torch.float64, device=x.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    ptr = lambda t: C.c_void_p(t.data_ptr())
+    rc = lib.la_alch_pairs_static(n, ptr(x), ptr(q), ptr(sigma), ptr(epsilon), ptr(alch), ptr(excl_group),
+                                  int(alch_idx.numel()), ptr(alch_idx), float(box), float(r_cut), float(eps_rf),
+                                  float(coul), float(lam), float(b_v), float(b_e), float(sc_alpha), int(sc_n),
+                                  int(sc_m), ptr(forces), ptr(out), C.c_void_p(stream.cuda_stream))
+    if rc < 0:
+        raise LabfError(rc, lib.la_static_last_error().decode())
+    return forces, out
