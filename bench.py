@@ -34,7 +34,7 @@ if ROOT not in sys.path:
 
 METRIC = "aggregate walker-ns/day"
 UNIT = "walker-ns/day"
-FLOP_PER_PAIR = 38  # FP32 flops per in-cutoff LJ+RF pair, force only (FMA = 2)
+FLOP_PER_PAIR = 37  # FP32 flops per in-cutoff LJ+RF pair, force only (FMA = 2); see k_pairs.cu
 WORKLOAD = ("solvation-like: 4096 flexible 3-site waters + 12-site alchemical solute "
             "(12300 atoms, 5 nm box, RF eps_rf=78, r_c=1.0 nm, skin 0.1 nm), 16 walkers "
             "(8 vdW-stage on [0,0.5] + 8 Coulomb-stage on [0.5,1]), 100 bins per stage, dt=1 fs, 300 K")
@@ -186,7 +186,9 @@ def gpu_arm(args):
         bench_step()
         flush_l2(flush)
     torch.cuda.synchronize()
-    launches0 = int(eng.stats()[2])
+    st0 = eng.stats()
+    launches0, rebuilds0 = int(st0[2]), int(st0[1])
+    list_entries, list_tiles = int(st0[5]), int(st0[6])
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist is not None:
         dist.barrier()
@@ -203,7 +205,9 @@ def gpu_arm(args):
         wall = time.perf_counter() - t0
     if dist is not None:
         dist.barrier()
-    launches = int(eng.stats()[2]) - launches0
+    st1 = eng.stats()
+    launches = int(st1[2]) - launches0
+    rebuild_rate = (int(st1[1]) - rebuilds0) / float(run.n_walkers * args.steps * md)
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if dist is not None:
@@ -291,6 +295,9 @@ def gpu_arm(args):
                         launch=eng.autotune_report()),
             pair_interactions_per_s=pair_rate,
             in_cutoff_pairs_per_md_step=pairs_per_md,
+            lists=dict(rebuilds_per_walker_md_step=rebuild_rate, cluster_pair_entries=list_entries,
+                       tiles_8x4=list_tiles, normal_pairs=pairs_n,
+                       tile_efficiency=pairs_n / max(1, 32 * list_tiles)),
             plain_form=dict(value=plain_val, unit=UNIT, md_steps=plain_md,
                             note="one walker per launch sequence, no CUDA graph"),
             e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,

@@ -272,7 +272,8 @@ int la_sync(la_handle *h, void *stream, uint32_t *status_bits);
  *   [3] in-cutoff normal pairs counted by the last LA_EF_COUNT_PAIRS call,
  *   [4] in-cutoff alchemical pairs counted by that call,
  *   [5] cluster-pair entries in the current lists (all walkers),
- *   [6] reserved (-1).
+ *   [6] 8 x 4 atom-pair tiles in the current lists (all walkers); each tile
+ *       is one warp-wide evaluation of 32 candidate pairs.
  * Synchronising.
  */
 #define LA_N_STATS 7

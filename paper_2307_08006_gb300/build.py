@@ -19,7 +19,9 @@ LIB = os.path.join(BUILD, "liblabf.so")
 SOURCES = ["labf_api.cu", "k_dyn.cu", "k_list.cu", "k_pairs.cu", "k_io.cu", "k_static.cu"]
 HEADERS = ["labf_internal.cuh", "labf_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
+# -ftz=true: FP32 denormals flush to zero (MD forces and positions never need
+# them; rsqrtf then maps to a single special-function instruction)
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-ftz=true", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I", CSRC, "-I", os.path.join(ROOT, "include")]
 
 

@@ -54,6 +54,7 @@ __global__ void k_integrate(Dev d, int w0, int w1, int g0, int g1) {
         const SysDev &S = d.sys[W.sys];
         unsigned long long *Fp = d.F + 3 * (size_t)g;
         float fx = fix_to_float(Fp[0]), fy = fix_to_float(Fp[1]), fz = fix_to_float(Fp[2]);
+        if (fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))) > FIX_LIMIT) set_status(d, LA_STATUS_FIXED_OVERFLOW);
         const float2 im = d.im[g];
         float4 v = d.vv[g];
         float4 x = d.xq[g];
@@ -96,7 +97,10 @@ __global__ void k_integrate(Dev d, int w0, int w1, int g0, int g1) {
         float dx = min_image(x.x - r.x, S.boxf, S.box_invf);
         float dy = min_image(x.y - r.y, S.boxf, S.box_invf);
         float dz = min_image(x.z - r.z, S.boxf, S.box_invf);
-        if (dx * dx + dy * dy + dz * dz > S.half_skin2) d.rebuild[w] = 1;
+        // all walkers of the system rebuild together: their rebuild kernels
+        // then run once, fully parallel, instead of on most steps
+        if (dx * dx + dy * dy + dz * dz > S.half_skin2)
+            for (int k = 0; k < S.w_count; ++k) d.rebuild[S.w_first + k] = 1;
     }
 }
 

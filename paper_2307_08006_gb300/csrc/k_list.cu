@@ -282,9 +282,13 @@ __global__ void k_permute_scatter(Dev d, int g0, int g1) {
             d.lj[g] = make_float2(ap.y, ap.z);
             d.im[g] = make_float2(ap.w, d.anoise[S.atom_off + a]);
             d.slot_of_atom[W.atom_base + a] = g;
+            d.smeta[g] = make_int2(d.agroup[S.atom_off + a], (int)d.aalch[S.atom_off + a]);
+            d.sexcl[g] = d.aexcl[S.atom_off + a];
         } else {
             d.lj[g] = make_float2(0.f, 0.f);
             d.im[g] = make_float2(0.f, 0.f);
+            d.smeta[g] = make_int2(-1, 1);
+            d.sexcl[g] = make_int4(-1, -1, -1, -1);
         }
         d.xq[g] = x;
         d.xref[g] = x;
@@ -292,8 +296,14 @@ __global__ void k_permute_scatter(Dev d, int g0, int g1) {
 }
 
 // -------------------------------------------------------------------------
-// R8: cluster-pair list.  One warp per super-cluster S; lane = ia + 8 jb
-// tests the pair (i-slot 8 ic + ia, j-slot 4 jc + jb) exactly.
+// R8: cluster-pair list.  One warp per (super-cluster S, candidate column
+// slot k): the k-th column (with its periodic image) within reach of S's box.
+// For every candidate super-cluster T of that column (cyclic half rule) T's
+// 64 slots are staged in shared memory, the 16 x 8 (j-cluster, i-cluster)
+// box tests run lane-parallel, and for each passing pair of clusters lane
+// (ia, jb) = (lane & 7, lane >> 3) tests the atom pair (8 ic + ia of S,
+// 4 jc + jb of T) exactly.  Entries go to the (S, k) sub-list; R8b
+// concatenates the sub-lists of S in k order.
 // -------------------------------------------------------------------------
 __device__ __forceinline__ long long bb_dist2(const int4 &alo, const int4 &ahi, const int4 &blo,
                                               const int4 &bhi, int sx, int sy, int sz) {
@@ -305,23 +315,27 @@ __device__ __forceinline__ long long bb_dist2(const int4 &alo, const int4 &ahi, 
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
-__device__ __forceinline__ bool excluded(const Dev &d, const SysDev &S, int a, int b) {
-    const int ga = d.agroup[S.atom_off + a];
-    if (ga >= 0 && ga == d.agroup[S.atom_off + b]) return true;
-    const int4 ea = d.aexcl[S.atom_off + a];
+// nonbonded exclusion of two real atoms (group, then extra partner lists)
+__device__ __forceinline__ bool excluded_meta(int a, int2 ma, int4 ea, int b, int2 mb, int4 eb) {
+    if (ma.x >= 0 && ma.x == mb.x) return true;
     if (ea.x == b || ea.y == b || ea.z == b || ea.w == b) return true;
-    const int4 eb = d.aexcl[S.atom_off + b];
     return eb.x == a || eb.y == a || eb.z == a || eb.w == a;
 }
 
-__global__ void __launch_bounds__(128) k_listbuild(Dev d, int w0, int w1) {
+constexpr int LB_WARPS = 4;
+
+__global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int w1) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int ia = lane & 7, jb = lane >> 3;
-    __shared__ int4 s_u[4][SC];
-    __shared__ int4 s_bb[4][2 * NIC + 2];
-    const int nwarp = gridDim.x * (blockDim.x >> 5);
+    __shared__ int4 s_u[LB_WARPS][SC], t_u[LB_WARPS][SC];
+    __shared__ int2 s_m[LB_WARPS][SC], t_m[LB_WARPS][SC];
+    __shared__ int4 s_e[LB_WARPS][SC], t_e[LB_WARPS][SC];
+    __shared__ int4 s_bb[LB_WARPS][2 * NIC + 2], t_bb[LB_WARPS][2 * NJC];
+    const long long nwarp = (long long)gridDim.x * LB_WARPS;
     const int s_begin = d.walk[w0].sc_off, s_end = d.walk[w1 - 1].sc_off + d.walk[w1 - 1].sc_cap;
-    for (int s = s_begin + blockIdx.x * (blockDim.x >> 5) + wib; s < s_end; s += nwarp) {
+    const long long total = (long long)(s_end - s_begin) * d.ncs;
+    for (long long idx = (long long)blockIdx.x * LB_WARPS + wib; idx < total; idx += nwarp) {
+        const int s = s_begin + (int)(idx / d.ncs), kslot = (int)(idx % d.ncs);
         int lo = w0, hi = w1 - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
@@ -333,111 +347,154 @@ __global__ void __launch_bounds__(128) k_listbuild(Dev d, int w0, int w1) {
         const SysDev &S = d.sys[W.sys];
         const int S_loc = s - W.sc_off;
         const int nsc = d.n_sc[w];
-        if (S_loc >= nsc) {
-            if (lane == 0) d.sc_nent[s] = 0;
-            continue;
-        }
-        const int gS = W.slot_off + S_loc * SC;
-        s_u[wib][lane] = d.uq[gS + lane];
-        s_u[wib][lane + 32] = d.uq[gS + lane + 32];
-        if (lane < 2 * NIC) s_bb[wib][lane] = d.bb_ic[2 * (size_t)s * NIC + lane];
-        if (lane < 2) s_bb[wib][2 * NIC + lane] = d.bb_sc[2 * (size_t)s + lane];
-        __syncwarp();
-        const int4 slo = s_bb[wib][2 * NIC], shi = s_bb[wib][2 * NIC + 1];
-        const long long R = S.R;
-        const int U = 1 << 24;
+        const size_t sub = (size_t)s * d.ncs + kslot;
+        const int4 slo = d.bb_sc[2 * (size_t)s], shi = d.bb_sc[2 * (size_t)s + 1];
         const int ncx = S.ncx;
         const int cx0 = (int)(((long long)(slo.x - S.Rq) * ncx) >> 24);
         const int cx1 = (int)(((long long)(shi.x + S.Rq) * ncx) >> 24);
         const int cy0 = (int)(((long long)(slo.y - S.Rq) * ncx) >> 24);
         const int cy1 = (int)(((long long)(shi.y + S.Rq) * ncx) >> 24);
+        const int cx = cx0 + kslot % S.cspan, cy = cy0 + kslot / S.cspan;
+        if (S_loc >= nsc || kslot >= S.cspan * S.cspan || cx > cx1 || cy > cy1) {
+            if (lane == 0) d.sub_n[sub] = 0;
+            continue;
+        }
+        if (kslot == 0 && lane == 0 && (cx1 - cx0 >= S.cspan || cy1 - cy0 >= S.cspan))
+            set_status(d, LA_STATUS_LIST_OVERFLOW);  // cannot happen for boxes inside a column
+        const int gS = W.slot_off + S_loc * SC;
+        __syncwarp();
+        for (int k = lane; k < SC; k += 32) {
+            s_u[wib][k] = d.uq[gS + k];
+            s_m[wib][k] = d.smeta[gS + k];
+            s_e[wib][k] = d.sexcl[gS + k];
+        }
+        if (lane < 2 * NIC) s_bb[wib][lane] = d.bb_ic[2 * (size_t)s * NIC + lane];
+        __syncwarp();
+        const long long R = S.R;
+        const int U = 1 << 24, H = 1 << 23;
+        const int ty = floordiv(cy, ncx), wy = cy - ty * ncx;
+        const int tx = floordiv(cx, ncx), wx = cx - tx * ncx;
+        const int col = wx + ncx * wy;
+        const int t0 = d.col_sc[W.col_off + col], tn = d.col_nsc[W.col_off + col];
         int nent = 0;
-        const size_t ebase = (size_t)s * d.ent_cap;
-        for (int cy = cy0; cy <= cy1; ++cy) {
-            const int ty = floordiv(cy, ncx), wy = cy - ty * ncx;
-            for (int cx = cx0; cx <= cx1; ++cx) {
-                const int tx = floordiv(cx, ncx), wx = cx - tx * ncx;
-                const int col = wx + ncx * wy;
-                const int t0 = d.col_sc[W.col_off + col], tn = d.col_nsc[W.col_off + col];
-                for (int T_loc = t0; T_loc < t0 + tn && T_loc < nsc; ++T_loc) {
-                    // cyclic half list over super-clusters: T is S's partner
-                    // when it lies less than half-way round the index circle
-                    if (T_loc != S_loc) {
-                        const int del = T_loc > S_loc ? T_loc - S_loc : T_loc - S_loc + nsc;
-                        if (2 * del > nsc || (2 * del == nsc && T_loc < S_loc)) continue;
-                    }
-                    const int t = W.sc_off + T_loc;
-                    const int4 tlo = d.bb_sc[2 * (size_t)t], thi = d.bb_sc[2 * (size_t)t + 1];
-                    if (tlo.w == 0) continue;
-                    for (int tz = -1; tz <= 1; ++tz) {
-                        if (T_loc == S_loc) {  // self: only shift 0 or lexicographically positive
-                            if (tx < 0 || (tx == 0 && (ty < 0 || (ty == 0 && tz < 0)))) continue;
-                        }
-                        const int shx = tx * U, shy = ty * U, shz = tz * U;
-                        if (bb_dist2(slo, shi, tlo, thi, shx, shy, shz) >= R) continue;
-                        const bool self0 = (T_loc == S_loc) && tx == 0 && ty == 0 && tz == 0;
-                        const int shift_code = (tx + 1) + 3 * (ty + 1) + 9 * (tz + 1);
-                        for (int jc = 0; jc < NJC; ++jc) {
-                            const int4 jlo = d.bb_jc[2 * ((size_t)t * NJC + jc)];
-                            if (jlo.w == 0) continue;
-                            const int4 jhi = d.bb_jc[2 * ((size_t)t * NJC + jc) + 1];
-                            if (bb_dist2(slo, shi, jlo, jhi, shx, shy, shz) >= R) continue;
-                            const int gj = W.slot_off + T_loc * SC + jc * JC + jb;
-                            const int4 uj = d.uq[gj];
-                            const bool jreal = uj.w >= 0 && !d.aalch[S.atom_off + max(uj.w, 0)];
-                            unsigned masks[NIC];
-                            unsigned imask = 0;
+        const size_t ebase = sub * d.sub_cap;
+        for (int T_loc = t0; T_loc < t0 + tn && T_loc < nsc; ++T_loc) {
+            // cyclic half list over super-clusters: T is S's partner when it
+            // lies less than half-way round the index circle
+            if (T_loc != S_loc) {
+                const int del = T_loc > S_loc ? T_loc - S_loc : T_loc - S_loc + nsc;
+                if (2 * del > nsc || (2 * del == nsc && T_loc < S_loc)) continue;
+            }
+            const int t = W.sc_off + T_loc;
+            const int4 tlo = d.bb_sc[2 * (size_t)t], thi = d.bb_sc[2 * (size_t)t + 1];
+            if (tlo.w == 0) continue;
+            unsigned zpass = 0;  // z shifts whose super-cluster boxes are in range
+            for (int tz = -1; tz <= 1; ++tz) {
+                if (T_loc == S_loc && (tx < 0 || (tx == 0 && (ty < 0 || (ty == 0 && tz < 0))))) continue;
+                if (bb_dist2(slo, shi, tlo, thi, tx * U, ty * U, tz * U) < R) zpass |= 1u << (tz + 1);
+            }
+            if (!zpass) continue;
+            const int gT = W.slot_off + T_loc * SC;
+            __syncwarp();
+            for (int k = lane; k < SC; k += 32) {
+                t_u[wib][k] = d.uq[gT + k];
+                t_m[wib][k] = d.smeta[gT + k];
+                t_e[wib][k] = d.sexcl[gT + k];
+            }
+            t_bb[wib][lane] = d.bb_jc[2 * (size_t)t * NJC + lane];
+            __syncwarp();
+            for (int tz = -1; tz <= 1; ++tz) {
+                if (!(zpass & (1u << (tz + 1)))) continue;
+                const int shx = tx * U, shy = ty * U, shz = tz * U;
+                const bool self0 = (T_loc == S_loc) && tx == 0 && ty == 0 && tz == 0;
+                const int shift_bits = (tx + 1) | ((ty + 1) << 2) | ((tz + 1) << 4);
+                unsigned cm[4];  // lane-parallel box tests of the 128 (jc, ic) combinations
 #pragma unroll
-                            for (int ic = 0; ic < NIC; ++ic) {
-                                masks[ic] = 0;
-                                const int4 ilo = s_bb[wib][2 * ic], ihi = s_bb[wib][2 * ic + 1];
-                                if (ilo.w == 0) continue;
-                                if (bb_dist2(ilo, ihi, jlo, jhi, shx, shy, shz) >= R) continue;
-                                const int4 ui = s_u[wib][ic * IC + ia];
-                                bool ok = jreal && ui.w >= 0;
-                                if (ok) ok = !d.aalch[S.atom_off + ui.w];
-                                if (ok && self0) ok = (ic * IC + ia) < (jc * JC + jb);
-                                if (ok) {
-                                    const int dx = uj.x + shx - ui.x, dy = uj.y + shy - ui.y, dz = uj.z + shz - ui.z;
-                                    const int H = 1 << 23;
-                                    ok = dx >= -H && dx < H && dy >= -H && dy < H && dz >= -H && dz < H;
-                                    if (ok) {
-                                        const long long D = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
-                                        ok = D < R;
-                                    }
-                                }
-                                if (ok) ok = !excluded(d, S, ui.w, uj.w);
-                                masks[ic] = __ballot_sync(0xffffffffu, ok);
-                                if (masks[ic]) imask |= 1u << ic;
-                            }
-                            if (imask) {
-                                if (nent < d.ent_cap) {
-                                    const size_t e = ebase + nent;
-                                    if (lane == 0)
-                                        d.ent_hdr[e] = make_int2(W.slot_off + T_loc * SC + jc * JC,
-                                                                 shift_code | (int)(imask << 8));
-                                    if (lane == 1)
-                                        d.ent_mask[2 * e] = make_uint4(masks[0], masks[1], masks[2], masks[3]);
-                                    if (lane == 2)
-                                        d.ent_mask[2 * e + 1] = make_uint4(masks[4], masks[5], masks[6], masks[7]);
-                                } else if (lane == 0) {
-                                    set_status(d, LA_STATUS_LIST_OVERFLOW);
-                                }
-                                ++nent;
-                            }
+                for (int q = 0; q < 4; ++q) {
+                    const int c = lane + 32 * q, jc = c >> 3, ic = c & 7;
+                    const int4 jlo = t_bb[wib][2 * jc], jhi = t_bb[wib][2 * jc + 1];
+                    const int4 ilo = s_bb[wib][2 * ic], ihi = s_bb[wib][2 * ic + 1];
+                    const bool ok = jlo.w > 0 && ilo.w > 0 && bb_dist2(ilo, ihi, jlo, jhi, shx, shy, shz) < R;
+                    cm[q] = __ballot_sync(0xffffffffu, ok);
+                }
+                for (int jc = 0; jc < NJC; ++jc) {
+                    const unsigned cand = (cm[jc >> 2] >> ((jc & 3) * 8)) & 0xffu;
+                    if (!cand) continue;
+                    const int4 uj = t_u[wib][jc * JC + jb];
+                    const int2 mj = t_m[wib][jc * JC + jb];
+                    const int4 ej = t_e[wib][jc * JC + jb];
+                    unsigned lbyte = 0, imask = 0;
+#pragma unroll
+                    for (int ic = 0; ic < NIC; ++ic) {
+                        if (!(cand & (1u << ic))) continue;
+                        const int si = ic * IC + ia;
+                        const int4 ui = s_u[wib][si];
+                        const int2 mi = s_m[wib][si];
+                        bool ok = ui.w >= 0 && uj.w >= 0 && !mi.y && !mj.y;
+                        if (self0) ok = ok && si < jc * JC + jb;
+                        const int dx = uj.x + shx - ui.x, dy = uj.y + shy - ui.y, dz = uj.z + shz - ui.z;
+                        ok = ok && dx >= -H && dx < H && dy >= -H && dy < H && dz >= -H && dz < H;
+                        if (ok) ok = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz < R;
+                        if (ok) ok = !excluded_meta(ui.w, mi, s_e[wib][si], uj.w, mj, ej);
+                        if (ok) lbyte |= 1u << ic;
+                        if (__any_sync(0xffffffffu, ok)) imask |= 1u << ic;
+                    }
+                    if (imask) {
+                        if (nent < d.sub_cap) {
+                            const size_t e = ebase + nent;
+                            if (lane == 0) d.sub_hdr[e] = make_int2(gT + jc * JC, shift_bits | (int)(imask << 8));
+                            d.sub_lb[32 * e + lane] = (unsigned char)lbyte;
+                        } else if (lane == 0) {
+                            set_status(d, LA_STATUS_LIST_OVERFLOW);
                         }
+                        ++nent;
                     }
                 }
             }
         }
-        if (lane == 0) d.sc_nent[s] = min(nent, d.ent_cap);
+        if (lane == 0) d.sub_n[sub] = min(nent, d.sub_cap);
         __syncwarp();
     }
 }
 
+// R8b: concatenate the sub-lists of each super-cluster in column-slot order
+__global__ void k_listcompact(Dev d, int w0, int w1) {
+    const int lane = threadIdx.x & 31;
+    const int nwarp = gridDim.x * (blockDim.x >> 5);
+    const int s_begin = d.walk[w0].sc_off, s_end = d.walk[w1 - 1].sc_off + d.walk[w1 - 1].sc_cap;
+    for (int s = s_begin + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < s_end; s += nwarp) {
+        int lo = w0, hi = w1 - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (d.walk[mid].sc_off <= s) lo = mid; else hi = mid - 1;
+        }
+        if (!d.rebuild[lo]) continue;
+        const size_t ebase = (size_t)s * d.ent_cap;
+        int n = 0;
+        for (int k = 0; k < d.ncs; ++k) {
+            const size_t sub = (size_t)s * d.ncs + k;
+            const int m = d.sub_n[sub];
+            for (int e = lane; e < m; e += 32) {
+                if (n + e >= d.ent_cap) break;
+                const size_t src = sub * d.sub_cap + e, dst = ebase + n + e;
+                d.ent_hdr[dst] = d.sub_hdr[src];
+                const uint4 *ps = reinterpret_cast<const uint4 *>(d.sub_lb + 32 * src);
+                uint4 *pd = reinterpret_cast<uint4 *>(d.ent_lb + 32 * dst);
+                pd[0] = ps[0];
+                pd[1] = ps[1];
+            }
+            n += m;
+        }
+        if (n > d.ent_cap && lane == 0) set_status(d, LA_STATUS_LIST_OVERFLOW);
+        if (lane == 0) d.sc_nent[s] = min(n, d.ent_cap);
+    }
+}
+
 // -------------------------------------------------------------------------
-// R9: alchemical list: one warp per (walker, alchemical atom) scans the
-// walker's slots in order (deterministic output order)
+// R9: alchemical list: one warp per (walker, alchemical atom).  Super-cluster
+// boxes are tested lane-parallel; the slots of the boxes in range are then
+// tested exactly, four slots per lane per pass, in super-cluster and slot
+// order (deterministic output order).
 // -------------------------------------------------------------------------
 __global__ void k_alchlist(Dev d, int w0, int w1, int a0, int a1) {
     const int lane = threadIdx.x & 31;
@@ -454,25 +511,61 @@ __global__ void k_alchlist(Dev d, int w0, int w1, int a0, int a1) {
         const SysDev &S = d.sys[W.sys];
         const int r = it - W.alch_base;
         const int a = d.alch_atoms[S.alch_off + r];
-        const int4 ua = d.uq[d.slot_of_atom[W.atom_base + a]];
+        const int ga = d.slot_of_atom[W.atom_base + a];
+        const int4 ua = d.uq[ga];
+        const int2 ma = d.smeta[ga];
+        const int4 ea = d.sexcl[ga];
+        const int U = 1 << 24;
         int cnt = 0;
-        const int nslots = d.n_sc[w] * SC;
+        const int nsc = d.n_sc[w];
         int *out = d.alch_slot + (size_t)it * d.alch_cap;
-        for (int k0 = 0; k0 < nslots; k0 += 32) {
-            const int g = W.slot_off + k0 + lane;
-            bool ok = false;
-            if (k0 + lane < nslots) {
-                const int4 ub = d.uq[g];
-                if (ub.w >= 0 && !d.aalch[S.atom_off + ub.w]) {
-                    const long long dx = torus_delta(ub.x, ua.x), dy = torus_delta(ub.y, ua.y),
-                                    dz = torus_delta(ub.z, ua.z);
-                    ok = dx * dx + dy * dy + dz * dz < S.R && !excluded(d, S, a, ub.w);
+        for (int b0 = 0; b0 < nsc; b0 += 32) {
+            // super-cluster box within the list radius of the atom (any image)
+            bool near = false;
+            if (b0 + lane < nsc) {
+                const size_t t = (size_t)(W.sc_off + b0 + lane);
+                const int4 tlo = d.bb_sc[2 * t], thi = d.bb_sc[2 * t + 1];
+                if (tlo.w > 0) {
+                    long long D = 0;
+                    const int uc[3] = {ua.x, ua.y, ua.z};
+                    const int lc[3] = {tlo.x, tlo.y, tlo.z}, hc[3] = {thi.x, thi.y, thi.z};
+                    for (int c = 0; c < 3; ++c) {
+                        long long best = -1;
+                        for (int sh = -1; sh <= 1; ++sh) {
+                            const long long gap = max(0, max(lc[c] + sh * U - uc[c], uc[c] - (hc[c] + sh * U)));
+                            if (best < 0 || gap < best) best = gap;
+                        }
+                        D += best * best;
+                    }
+                    near = D < S.R;
                 }
             }
-            const unsigned m = __ballot_sync(0xffffffffu, ok);
-            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-            if (ok && pos < d.alch_cap) out[pos] = g;
-            cnt += __popc(m);
+            unsigned nm = __ballot_sync(0xffffffffu, near);
+            while (nm) {
+                const int k = __ffs(nm) - 1;
+                nm &= nm - 1;
+                const int gbase = W.slot_off + (b0 + k) * SC;
+                bool ok[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int g = gbase + lane + 32 * h;
+                    const int4 ub = d.uq[g];
+                    const int2 mb = d.smeta[g];
+                    ok[h] = false;
+                    if (ub.w >= 0 && !mb.y) {
+                        const long long dx = torus_delta(ub.x, ua.x), dy = torus_delta(ub.y, ua.y),
+                                        dz = torus_delta(ub.z, ua.z);
+                        ok[h] = dx * dx + dy * dy + dz * dz < S.R && !excluded_meta(a, ma, ea, ub.w, mb, d.sexcl[g]);
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const unsigned m = __ballot_sync(0xffffffffu, ok[h]);
+                    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                    if (ok[h] && pos < d.alch_cap) out[pos] = gbase + lane + 32 * h;
+                    cnt += __popc(m);
+                }
+            }
         }
         if (cnt > d.alch_cap) {
             if (lane == 0) set_status(d, LA_STATUS_ALCH_OVERFLOW);
@@ -538,6 +631,28 @@ __global__ void k_items(Dev d, int w0) {
 }
 
 // -------------------------------------------------------------------------
+// gate of the rebuild chain inside a CUDA graph: one thread sets the step's
+// conditional handle to "some walker must rebuild", so that the graph skips
+// the whole chain otherwise; rebuild events are counted in counters[6]
+// -------------------------------------------------------------------------
+__global__ void k_gate(Dev d, int w0, int w1, cudaGraphConditionalHandle handle) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int w = w0 + threadIdx.x; w < w1; w += blockDim.x)
+        if (d.rebuild[w]) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cudaGraphSetConditional(handle, any ? 1u : 0u);
+        if (any) atomicAdd(&d.counters[6], 1ull);
+    }
+}
+
+void launch_gate(const Dev &d, int w0, int w1, cudaGraphConditionalHandle handle, cudaStream_t s) {
+    k_gate<<<1, 256, 0, s>>>(d, w0, w1, handle);
+}
+
+// -------------------------------------------------------------------------
 // host launcher of the whole rebuild chain (every kernel exits early for
 // walkers whose rebuild flag is clear)
 // -------------------------------------------------------------------------
@@ -561,7 +676,12 @@ void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream
     k_kdsplit<<<kb, 128, 0, s>>>(d, w0, w1);
     k_permute_gather<<<sb, 256, 0, s>>>(d, g0, g1);
     k_permute_scatter<<<sb, 256, 0, s>>>(d, g0, g1);
-    k_listbuild<<<kb, 128, 0, s>>>(d, w0, w1);
+    {
+        long long nlb = ((long long)nsc * hv.ncs + LB_WARPS - 1) / LB_WARPS;
+        int lb = (int)(nlb < (long long)hv.n_sm * 32 ? nlb : (long long)hv.n_sm * 32);
+        k_listbuild<<<lb < 1 ? 1 : lb, LB_WARPS * 32, 0, s>>>(d, w0, w1);
+        k_listcompact<<<kb, 128, 0, s>>>(d, w0, w1);
+    }
     if (a1 > a0) {
         int ab = (a1 - a0 + 3) / 4;
         ab = ab > hv.n_sm * 8 ? hv.n_sm * 8 : ab;
@@ -572,7 +692,7 @@ void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream
 
 int rebuild_kernel_count(const HostView &hv, int w0, int w1) {
     const int a0 = hv.alch_base[w0], a1 = hv.alch_base[w1 - 1] + hv.n_alch[w1 - 1];
-    return a1 > a0 ? 10 : 9;
+    return a1 > a0 ? 11 : 10;
 }
 
 }  // namespace labf

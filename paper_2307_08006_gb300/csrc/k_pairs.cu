@@ -3,20 +3,22 @@
 // scaled pairs with the walker's dU/dlambda partials (Sec. 3.1.2, Eq.
 // lambda-abf: the engine provides dV/dlambda every step).
 //
-// Normal pairs: one warp per work item (a chunk of one super-cluster's
-// j-list).  The super-cluster's 64 slots sit in shared memory; lane
-// (ia, jb) = (lane & 7, lane >> 3) owns i-atom ia of each i-cluster and
-// j-atom jb of the current j-cluster.  For each entry the warp loops over
-// the i-clusters flagged in the entry, so one j-cluster load and one j-force
-// reduction serve up to 8 x 32 pairs; the eight i-force accumulators stay in
-// registers for the whole item.  Forces are accumulated in FP32 and added to
-// the 64-bit fixed-point force array with integer atomics (order-free, so
-// results are bit-reproducible).
+// Normal pairs: warps take work items (a chunk of one super-cluster's
+// j-list) from a global counter.  The super-cluster's 64 slots sit in shared
+// memory.  Entries are prepared 32 at a time, one per lane (header, periodic
+// shift applied to the 4 j-atoms, lane mask bytes), into shared memory; then
+// for each entry lane (ia, jb) = (lane & 7, lane >> 3) evaluates the pair
+// (i-atom ia of every flagged i-cluster, j-atom jb).  One j-cluster load and
+// one j-force reduction serve up to 8 x 32 pairs, and the eight i-force
+// accumulators stay in registers for the whole item.  Forces are summed in
+// FP32 and added to the 64-bit fixed-point force array with integer atomics
+// (order-free, so results are bit-reproducible).
 //
-// Per in-cutoff pair (force only), 38 FP32 flops (FMA = 2) plus one rsqrt:
-//   d = x_i - x_j (3), r2 (5), 1/r2 (1), sigma_ij = s_i + s_j, its square,
-//   (sigma/r)^2, ^6 (5), 4 eps_ij (1), 4eps (sigma/r)^6 (12 (sigma/r)^6 - 6)/r2
-//   (5), q_i q_j (1/r^3 - 2 k_rf) (4), sum (1), f_i += f d, f_j -= f d (12).
+// Per in-cutoff pair (force only), 37 FP32 flops (FMA = 2) plus one rsqrt:
+//   d = x_i - x_j (3), r2 (5), 1/r2 (1), sigma_ij = s_i + s_j, (sigma/r)^2,
+//   (sigma/r)^6 (5), 4 eps_ij (sigma/r)^6 (2), t = 12 (sigma/r)^6 - 6 (2),
+//   b = q_i q_j / r + 4eps (sigma/r)^6 t (4), f = b / r2 - 2 k_rf q_i q_j (3),
+//   f_i += f d, f_j -= f d (12).
 //
 // Alchemical pairs: one warp per (walker, alchemical atom); lanes stride over
 // its environment list.  Soft-core LJ lambda_v^n 4 eps (s^-2 - s^-1) with
@@ -29,39 +31,49 @@
 namespace labf {
 
 constexpr int PAIR_WARPS = 8;
+constexpr int EPC = 32;  // entries prepared per pass (one per lane)
+constexpr unsigned FULL = 0xffffffffu;
 
-template <int IC_>
-__device__ __forceinline__ unsigned pick_mask(const uint4 &m0, const uint4 &m1) {
-    return IC_ == 0 ? m0.x : IC_ == 1 ? m0.y : IC_ == 2 ? m0.z : IC_ == 3 ? m0.w
-         : IC_ == 4 ? m1.x : IC_ == 5 ? m1.y : IC_ == 6 ? m1.z : m1.w;
-}
+struct PairShared {
+    float4 sxq[PAIR_WARPS][SC];      // the item's super-cluster
+    float2 slj[PAIR_WARPS][SC];
+    float4 jx[PAIR_WARPS][EPC][JC];  // prepared j-atoms (shift applied)
+    float2 jl[PAIR_WARPS][EPC][JC];
+    unsigned char lb[PAIR_WARPS][EPC][32];
+    int pre[LA_MAX_WALKERS_PER_LAUNCH + 1];
+};
+
+// counters[4] hands out work items; counters[5] counts warps that found no
+// more work; the last one resets both for the next launch
+constexpr int CTR_ITEM = 4, CTR_DONE = 5;
 
 template <bool ENERGY>
-__device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int nblk, float4 (*sxq)[SC],
-                                             float2 (*slj)[SC], const int *pre) {
+__device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int nblk, PairShared &sh) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int ia = lane & 7, jb = lane >> 3;
     const int nw = w1 - w0;
-    const int total = pre[nw];
-    const int nwarps = nblk * PAIR_WARPS;
-    for (int v = blockIdx.x * PAIR_WARPS + wib; v < total; v += nwarps) {
+    const int total = sh.pre[nw];
+    for (;;) {
+        int v = 0;
+        if (lane == 0) v = (int)atomicAdd(&d.counters[CTR_ITEM], 1ull);
+        v = __shfl_sync(FULL, v, 0);
+        if (v >= total) break;
         int lo = 0, hi = nw - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (pre[mid] <= v) lo = mid; else hi = mid - 1;
+            if (sh.pre[mid] <= v) lo = mid; else hi = mid - 1;
         }
         const int w = w0 + lo;
         const WalkerDev &W = d.walk[w];
         const SysDev &S = d.sys[W.sys];
-        const int4 it = d.items[W.item_base + (v - pre[lo])];
+        const int4 it = d.items[W.item_base + (v - sh.pre[lo])];
         const int sc = it.x;
         const int gS = W.slot_off + (sc - W.sc_off) * SC;
         __syncwarp();
-        sxq[wib][lane] = d.xq[gS + lane];
-        sxq[wib][lane + 32] = d.xq[gS + lane + 32];
-        slj[wib][lane] = d.lj[gS + lane];
-        slj[wib][lane + 32] = d.lj[gS + lane + 32];
-        __syncwarp();
+        sh.sxq[wib][lane] = d.xq[gS + lane];
+        sh.sxq[wib][lane + 32] = d.xq[gS + lane + 32];
+        sh.slj[wib][lane] = d.lj[gS + lane];
+        sh.slj[wib][lane + 32] = d.lj[gS + lane + 32];
         const float L = S.boxf, rc2 = S.rc2, krf2 = 2.0f * S.krf, krf = S.krf, crf = S.crf;
         float fi[NIC][3];
 #pragma unroll
@@ -70,75 +82,88 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
         float elj = 0.f, erf = 0.f;
         int npair = 0;
         const size_t ebase = (size_t)sc * d.ent_cap;
-        for (int e = it.y; e < it.z; ++e) {
-            const int2 hdr = d.ent_hdr[ebase + e];
-            const uint4 m0 = d.ent_mask[2 * (ebase + e)], m1 = d.ent_mask[2 * (ebase + e) + 1];
-            const int gj = hdr.x + jb;
-            float4 xj = d.xq[gj];
-            const float2 lj_j = d.lj[gj];
-            const int code = hdr.y & 255;
-            const int sx = code % 3 - 1, sy = (code / 3) % 3 - 1, sz = code / 9 - 1;
-            xj.x += (float)sx * L;
-            xj.y += (float)sy * L;
-            xj.z += (float)sz * L;
-            const unsigned imask = (unsigned)hdr.y >> 8;
-            touched |= imask;
-            float fjx = 0.f, fjy = 0.f, fjz = 0.f;
+        for (int eb = it.y; eb < it.z; eb += EPC) {
+            const int ne = min(EPC, it.z - eb);
+            // prepare up to 32 entries, one per lane
+            int gj_l = 0;
+            unsigned im_l = 0;
+            __syncwarp();
+            if (lane < ne) {
+                const int2 hdr = d.ent_hdr[ebase + eb + lane];
+                gj_l = hdr.x;
+                im_l = ((unsigned)hdr.y >> 8) & 0xffu;
+                const float sx = (float)((hdr.y & 3) - 1) * L;
+                const float sy = (float)(((hdr.y >> 2) & 3) - 1) * L;
+                const float sz = (float)(((hdr.y >> 4) & 3) - 1) * L;
 #pragma unroll
-            for (int ic = 0; ic < NIC; ++ic) {
-                if (imask & (1u << ic)) {
-                    unsigned m;
-                    switch (ic) {
-                        case 0: m = pick_mask<0>(m0, m1); break;
-                        case 1: m = pick_mask<1>(m0, m1); break;
-                        case 2: m = pick_mask<2>(m0, m1); break;
-                        case 3: m = pick_mask<3>(m0, m1); break;
-                        case 4: m = pick_mask<4>(m0, m1); break;
-                        case 5: m = pick_mask<5>(m0, m1); break;
-                        case 6: m = pick_mask<6>(m0, m1); break;
-                        default: m = pick_mask<7>(m0, m1); break;
-                    }
-                    const float4 xi = sxq[wib][ic * IC + ia];
-                    const float2 li = slj[wib][ic * IC + ia];
-                    const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const bool in = ((m >> lane) & 1u) && (r2 < rc2);
-                    const float rinv = rsqrtf(r2);
-                    const float r2inv = rinv * rinv;
-                    const float sg = li.x + lj_j.x;
-                    const float sr2 = sg * sg * r2inv;
-                    const float sr6 = sr2 * sr2 * sr2;
-                    const float e4 = li.y * lj_j.y;
-                    const float flj = e4 * sr6 * fmaf(12.f, sr6, -6.f) * r2inv;
-                    const float qq = xi.w * xj.w;
-                    const float frf = qq * (rinv * r2inv - krf2);
-                    float fs = flj + frf;
-                    fs = in ? fs : 0.f;
-                    fi[ic][0] = fmaf(fs, dx, fi[ic][0]);
-                    fi[ic][1] = fmaf(fs, dy, fi[ic][1]);
-                    fi[ic][2] = fmaf(fs, dz, fi[ic][2]);
-                    fjx = fmaf(-fs, dx, fjx);
-                    fjy = fmaf(-fs, dy, fjy);
-                    fjz = fmaf(-fs, dz, fjz);
-                    if (ENERGY) {
-                        if (in) {
-                            elj += e4 * sr6 * (sr6 - 1.f);
-                            erf += qq * (rinv + krf * r2 - crf);
-                            ++npair;
+                for (int q = 0; q < JC; ++q) {
+                    float4 x = d.xq[gj_l + q];
+                    x.x += sx;
+                    x.y += sy;
+                    x.z += sz;
+                    sh.jx[wib][lane][q] = x;
+                    sh.jl[wib][lane][q] = d.lj[gj_l + q];
+                }
+                const uint4 *src = reinterpret_cast<const uint4 *>(d.ent_lb + 32 * (ebase + eb + lane));
+                uint4 *dst = reinterpret_cast<uint4 *>(&sh.lb[wib][lane][0]);
+                dst[0] = src[0];
+                dst[1] = src[1];
+            }
+            __syncwarp();
+            for (int k = 0; k < ne; ++k) {
+                const unsigned imask = __shfl_sync(FULL, im_l, k);
+                const int gj = __shfl_sync(FULL, gj_l, k) + jb;
+                const float4 xj = sh.jx[wib][k][jb];
+                const float2 lj_j = sh.jl[wib][k][jb];
+                const unsigned lb = sh.lb[wib][k][lane];
+                touched |= imask;
+                float fjx = 0.f, fjy = 0.f, fjz = 0.f;
+#pragma unroll
+                for (int ic = 0; ic < NIC; ++ic) {
+                    if (imask & (1u << ic)) {
+                        const float4 xi = sh.sxq[wib][ic * IC + ia];
+                        const float2 li = sh.slj[wib][ic * IC + ia];
+                        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const bool in = (lb & (1u << ic)) && (r2 < rc2);
+                        const float rinv = rsqrtf(r2);
+                        const float r2inv = rinv * rinv;
+                        const float sg = li.x + lj_j.x;
+                        const float sr2 = sg * sg * r2inv;
+                        const float sr6 = sr2 * sr2 * sr2;
+                        const float e4s6 = li.y * lj_j.y * sr6;
+                        const float qq = xi.w * xj.w;
+                        const float b = fmaf(qq, rinv, e4s6 * fmaf(12.f, sr6, -6.f));
+                        float fs = fmaf(b, r2inv, -qq * krf2);
+                        fs = in ? fs : 0.f;
+                        fi[ic][0] = fmaf(fs, dx, fi[ic][0]);
+                        fi[ic][1] = fmaf(fs, dy, fi[ic][1]);
+                        fi[ic][2] = fmaf(fs, dz, fi[ic][2]);
+                        fjx = fmaf(-fs, dx, fjx);
+                        fjy = fmaf(-fs, dy, fjy);
+                        fjz = fmaf(-fs, dz, fjz);
+                        if (ENERGY) {
+                            if (in) {
+                                elj += e4s6 * (sr6 - 1.f);
+                                erf += qq * (rinv + krf * r2 - crf);
+                                ++npair;
+                            }
                         }
                     }
                 }
-            }
-            // j-force: sum over the 8 i-lanes of each j-atom
-#pragma unroll
-            for (int o = 1; o < 8; o <<= 1) {
-                fjx += __shfl_xor_sync(0xffffffffu, fjx, o);
-                fjy += __shfl_xor_sync(0xffffffffu, fjy, o);
-                fjz += __shfl_xor_sync(0xffffffffu, fjz, o);
-            }
-            if (ia < 3) {
-                const float f = ia == 0 ? fjx : (ia == 1 ? fjy : fjz);
-                atomicAdd(d.F + 3 * (size_t)gj + ia, (unsigned long long)__float2ll_rn(f * F_TO_FIX));
+                // j-force: sum over the 8 i-lanes of each j-atom, transposed so
+                // that lanes ia = 0, 2, 4 of the group end with x, y, z
+                const bool b2 = (ia & 4) != 0, b1 = (ia & 2) != 0;
+                const float p0 = b2 ? fjx : fjz, p1 = b2 ? fjy : 0.f;
+                const float q0 = __shfl_xor_sync(FULL, p0, 4);
+                const float q1 = __shfl_xor_sync(FULL, p1, 4);
+                const float a0 = (b2 ? fjz : fjx) + q0;
+                const float a1 = (b2 ? 0.f : fjy) + q1;
+                const float q2 = __shfl_xor_sync(FULL, b1 ? a0 : a1, 2);
+                float c = (b1 ? a1 : a0) + q2;
+                c += __shfl_xor_sync(FULL, c, 1);
+                if ((ia & 1) == 0 && ia < 6)
+                    atomicAdd(d.F + 3 * (size_t)gj + (ia >> 1), (unsigned long long)__float2ll_rn(c * F_TO_FIX));
             }
         }
         // i-forces: sum over the 4 j-lanes; lane (ia, jb) writes i-clusters 2jb, 2jb+1
@@ -146,15 +171,14 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
         for (int ic = 0; ic < NIC; ++ic) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                fi[ic][c] += __shfl_xor_sync(0xffffffffu, fi[ic][c], 8);
-                fi[ic][c] += __shfl_xor_sync(0xffffffffu, fi[ic][c], 16);
+                fi[ic][c] += __shfl_xor_sync(FULL, fi[ic][c], 8);
+                fi[ic][c] += __shfl_xor_sync(FULL, fi[ic][c], 16);
             }
         }
 #pragma unroll
         for (int ic = 0; ic < NIC; ++ic) {
             if ((ic >> 1) == jb && (touched & (1u << ic))) {
-                const int gi = gS + ic * IC + ia;
-                unsigned long long *p = d.F + 3 * (size_t)gi;
+                unsigned long long *p = d.F + 3 * (size_t)(gS + ic * IC + ia);
                 atomicAdd(p + 0, (unsigned long long)__float2ll_rn(fi[ic][0] * F_TO_FIX));
                 atomicAdd(p + 1, (unsigned long long)__float2ll_rn(fi[ic][1] * F_TO_FIX));
                 atomicAdd(p + 2, (unsigned long long)__float2ll_rn(fi[ic][2] * F_TO_FIX));
@@ -164,7 +188,7 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
             const double el = warp_sum((double)elj), er = warp_sum((double)erf);
             int np = npair;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(0xffffffffu, np, o);
+            for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(FULL, np, o);
             if (lane == 0) {
                 atomicAdd((unsigned long long *)&d.eterm[N_ETERMS * w + 0],
                           (unsigned long long)__double2ll_rn(el * E_TO_FIX));
@@ -172,6 +196,16 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
                           (unsigned long long)__double2ll_rn(er * E_TO_FIX));
                 atomicAdd(&d.counters[1], (unsigned long long)np);
             }
+        }
+    }
+    // the last warp out resets the work counters for the next launch
+    if (lane == 0) {
+        __threadfence();
+        const unsigned long long done = atomicAdd(&d.counters[CTR_DONE], 1ull);
+        if (done == (unsigned long long)nblk * PAIR_WARPS - 1ull) {
+            d.counters[CTR_ITEM] = 0ull;
+            d.counters[CTR_DONE] = 0ull;
+            __threadfence();
         }
     }
 }
@@ -276,7 +310,7 @@ __device__ __forceinline__ void alch_items(const Dev &d, int w0, int w1, int a0,
         }
         if (ENERGY) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) npair += __shfl_xor_sync(0xffffffffu, npair, o);
+            for (int o = 16; o > 0; o >>= 1) npair += __shfl_xor_sync(FULL, npair, o);
         }
         if (lane == 0) {
             add_force(d, ga, fax, fay, faz);
@@ -294,11 +328,11 @@ __device__ __forceinline__ void alch_items(const Dev &d, int w0, int w1, int a0,
     }
 }
 
-template <bool ENERGY>
-__global__ void __launch_bounds__(PAIR_WARPS * 32) k_pairs(Dev d, int w0, int w1, int nblk_pairs, int a0, int a1) {
-    __shared__ float4 sxq[PAIR_WARPS][SC];
-    __shared__ float2 slj[PAIR_WARPS][SC];
-    __shared__ int pre[LA_MAX_WALKERS_PER_LAUNCH + 1];
+// MINB: resident CTAs per SM the register allocation is sized for (the
+// autotuner picks 3, spill-free, or 4, more warps to hide latency)
+template <bool ENERGY, int MINB>
+__global__ void __launch_bounds__(PAIR_WARPS * 32, MINB) k_pairs(Dev d, int w0, int w1, int nblk_pairs, int a0, int a1) {
+    __shared__ PairShared sh;
     if (blockIdx.x >= nblk_pairs) {
         alch_items<ENERGY>(d, w0, w1, a0, a1, blockIdx.x - nblk_pairs, gridDim.x - nblk_pairs);
         return;
@@ -306,13 +340,13 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32) k_pairs(Dev d, int w0, int w1
     if (threadIdx.x == 0) {
         int acc = 0;
         for (int w = w0; w < w1; ++w) {
-            pre[w - w0] = acc;
+            sh.pre[w - w0] = acc;
             acc += d.n_items[w];
         }
-        pre[w1 - w0] = acc;
+        sh.pre[w1 - w0] = acc;
     }
     __syncthreads();
-    normal_items<ENERGY>(d, w0, w1, nblk_pairs, sxq, slj, pre);
+    normal_items<ENERGY>(d, w0, w1, nblk_pairs, sh);
 }
 
 void launch_pairs(const Dev &d, const HostView &hv, int w0, int w1, bool energy, cudaStream_t s) {
@@ -326,8 +360,9 @@ void launch_pairs(const Dev &d, const HostView &hv, int w0, int w1, bool energy,
     }
     const int a0 = hv.alch_base[w0], a1 = hv.alch_base[w1 - 1] + hv.n_alch[w1 - 1];
     int ablk = (a1 - a0 + PAIR_WARPS - 1) / PAIR_WARPS;
-    if (energy) k_pairs<true><<<nblk + ablk, PAIR_WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1);
-    else k_pairs<false><<<nblk + ablk, PAIR_WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1);
+    if (energy) k_pairs<true, 3><<<nblk + ablk, PAIR_WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1);
+    else if (hv.pair_minb >= 4) k_pairs<false, 4><<<nblk + ablk, PAIR_WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1);
+    else k_pairs<false, 3><<<nblk + ablk, PAIR_WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1);
 }
 
 }  // namespace labf

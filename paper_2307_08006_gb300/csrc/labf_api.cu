@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -23,7 +24,7 @@ constexpr size_t ALIGN = 256;
 constexpr int IO_FLOATS_MIN = 1 << 16;
 
 struct SysLayout {
-    int n, n_alch, ncx, n_cols, sc_cap, slot_cap, W, P;
+    int n, n_alch, ncx, n_cols, sc_cap, slot_cap, W, P, Rq, cspan;
     double rho, r_list;
 };
 
@@ -32,7 +33,7 @@ struct Layout {
     int W = 0, n_stages = 0, total_bins = 0, max_bins = 0, P_max = 1;
     long long slots = 0, scs = 0, cols = 0, atoms_w = 0, alch_w = 0, items = 0, bo = 0;
     long long atoms_s = 0, alch_s = 0, bonds = 0, angles = 0, posres = 0, fb = 0, lh = 0;
-    int ent_cap = 0, alch_cap = 0, chunk = 32, max_n = 0;
+    int ent_cap = 0, alch_cap = 0, chunk = 32, max_n = 0, ncs = 1, sub_cap = 0;
     size_t bytes = 0;
 };
 
@@ -129,7 +130,7 @@ void compute_layout(const la_system_desc *sys, int n_sys, const la_options *opt,
     const double fac = (opt && opt->list_capacity_factor >= 1.0) ? opt->list_capacity_factor : 1.6;
     L.chunk = (opt && opt->chunk_entries > 0) ? opt->chunk_entries : 32;
     const double pi = 3.14159265358979323846;
-    double ent_est = 0.0, alch_est = 0.0;
+    double ent_est = 0.0, alch_est = 0.0, sub_est = 0.0;
     for (int s = 0; s < n_sys; ++s) {
         const la_system_desc &S = sys[s];
         SysLayout sl{};
@@ -152,6 +153,15 @@ void compute_layout(const la_system_desc *sys, int n_sys, const la_options *opt,
         const double V = steiner_box(wc + ej, wc + ej, h + ej, sl.r_list);
         const double full = std::min(sl.rho * V / JC, 27.0 * sl.sc_cap * NJC);
         ent_est = std::max(ent_est, full);
+        // list radius in quantized units and the candidate columns per
+        // dimension: a super-cluster box lies inside one column, so at most
+        // floor(3 + 2 Rq ncx / 2^24) columns are within reach
+        sl.Rq = (int)std::ceil(sl.r_list / S.box * 16777216.0) + 1;
+        sl.cspan = (int)std::floor(3.0 + 2.0 * sl.Rq * (double)sl.ncx / 16777216.0);
+        L.ncs = std::max(L.ncs, sl.cspan * sl.cspan);
+        const double col_jc = sl.rho * wc * wc * (h + 2.0 * sl.r_list + 2.0 * ej) / JC;
+        const double col_cap = 3.0 * NJC * (sl.rho * wc * wc * S.box / SC + 2.0);
+        sub_est = std::max(sub_est, std::min(col_jc, col_cap));
         alch_est = std::max(alch_est, sl.rho * 4.0 / 3.0 * pi * std::pow(sl.r_list, 3));
         L.sys.push_back(sl);
         L.W += sl.W;
@@ -179,6 +189,7 @@ void compute_layout(const la_system_desc *sys, int n_sys, const la_options *opt,
     // the cyclic half list gives each super-cluster about half its neighbourhood
     L.ent_cap = (int)std::ceil(fac * 0.6 * ent_est) + 64;
     L.alch_cap = ((int)std::ceil(fac * alch_est) + 64 + 31) / 32 * 32;
+    L.sub_cap = ((int)std::ceil(fac * sub_est) + 32 + 31) / 32 * 32;
     const int chunks = (L.ent_cap + L.chunk - 1) / L.chunk;
     L.items = L.scs * chunks;
 }
@@ -215,6 +226,8 @@ size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io
     d.slot_walker = a.take<int>(L.slots);
     d.F = a.take<unsigned long long>(3 * L.slots);
     d.uq = a.take<int4>(L.slots);
+    d.smeta = a.take<int2>(L.slots);
+    d.sexcl = a.take<int4>(L.slots);
     d.t_xq = a.take<float4>(L.slots);
     d.t_vv = a.take<float4>(L.slots);
     d.t_old = a.take<int>(L.slots);
@@ -235,7 +248,10 @@ size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io
     d.bb_jc = a.take<int4>(2 * L.scs * NJC);
     d.sc_nent = a.take<int>(L.scs);
     d.ent_hdr = a.take<int2>(L.scs * (long long)L.ent_cap);
-    d.ent_mask = a.take<uint4>(2 * L.scs * (long long)L.ent_cap);
+    d.ent_lb = a.take<unsigned char>(32 * L.scs * (long long)L.ent_cap);
+    d.sub_hdr = a.take<int2>(L.scs * (long long)L.ncs * L.sub_cap);
+    d.sub_lb = a.take<unsigned char>(32 * L.scs * (long long)L.ncs * L.sub_cap);
+    d.sub_n = a.take<int>(L.scs * (long long)L.ncs);
     d.items = a.take<int4>(L.items);
     d.n_items = a.take<int>(L.W);
     d.alch_cnt = a.take<int>(std::max<long long>(1, L.alch_w));
@@ -287,7 +303,8 @@ struct la_handle {
     la_options opt{};
     int graph_steps = 10;
     cudaGraphExec_t graph = nullptr;
-    cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+    long long graph_launches_per_step = 0;
     int n_sm = 0;
     unsigned *h_status = nullptr;  // pinned
     cudaEvent_t status_ev = nullptr;
@@ -409,14 +426,50 @@ int capture_graph(la_handle *h) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
     }
+    // Each step: integrate -> gate -> IF(some walker must rebuild){rebuild
+    // chain} -> pairs, bonded, walker, lambda.  The gate kernel sets the
+    // step's conditional handle, so steps without a rebuild launch no list
+    // kernel at all.
+    const int W = h->L.W;
+    cudaStream_t cs = h->cap_stream, cb = h->cap_stream2;
     cudaGraph_t g;
-    CU(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < h->graph_steps; ++k) enqueue_step(h, 0, h->L.W, h->cap_stream);
-    CU(h, cudaStreamEndCapture(h->cap_stream, &g));
+    CU(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < h->graph_steps; ++k) {
+        launch_integrate(h->d, h->hv, 0, W, cs);
+        cudaStreamCaptureStatus st;
+        cudaGraph_t cg;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        CU(h, cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle hc;
+        CU(h, cudaGraphConditionalHandleCreate(&hc, cg, 0, cudaGraphCondAssignDefault));
+        launch_gate(h->d, 0, W, hc, cs);
+        CU(h, cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, &deps, nullptr, &nd));
+        cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+        p.conditional.handle = hc;
+        p.conditional.type = cudaGraphCondTypeIf;
+        p.conditional.size = 1;
+        cudaGraphNode_t cn;
+        CU(h, cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &p));
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        CU(h, cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        launch_rebuild(h->d, h->hv, 0, W, cb);
+        cudaGraph_t body_out;
+        CU(h, cudaStreamEndCapture(cb, &body_out));
+        CU(h, cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+        launch_pairs(h->d, h->hv, 0, W, false, cs);
+        launch_bonded(h->d, h->hv, 0, W, false, cs);
+        launch_walker(h->d, 0, W, false, cs);
+        launch_lambda(h->d, 0, (int)h->stages.size(), false, cs);
+    }
+    CU(h, cudaStreamEndCapture(cs, &g));
     cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, LA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
     h->launches_per_step = kernels_per_step(h);
+    // graph steps: integrate, gate, pairs, walker, lambda (+ bonded); list
+    // kernels are counted per executed rebuild (device counter)
+    h->graph_launches_per_step = h->launches_per_step - rebuild_kernel_count(h->hv, 0, W) + 1;
     return LA_OK;
 }
 
@@ -438,8 +491,9 @@ int time_steps(la_handle *h, int n, cudaStream_t s, float *ms) {
     return e == cudaSuccess ? LA_OK : fail(h, LA_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
 }
 
-std::map<std::string, std::pair<int, int>> &tune_cache() {
-    static std::map<std::string, std::pair<int, int>> c;
+// autotuner results per (device, system shape): CTAs/SM, entries/item, register split
+std::map<std::string, std::array<int, 3>> &tune_cache() {
+    static std::map<std::string, std::array<int, 3>> c;
     return c;
 }
 
@@ -499,6 +553,8 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
     d.n_walkers = L.W;
     d.n_stages = L.n_stages;
     d.ent_cap = L.ent_cap;
+    d.ncs = L.ncs;
+    d.sub_cap = L.sub_cap;
     d.alch_cap = L.alch_cap;
     d.max_bins = L.max_bins;
     d.P_max = L.P_max;
@@ -564,8 +620,9 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         const double binv = 1.0 / S.box;
         const double a_ = sl.r_list * binv;
         D.R = (long long)std::floor((a_ * a_) * 281474976710656.0);
-        D.Rq = (int)std::ceil(a_ * 16777216.0) + 1;
+        D.Rq = sl.Rq;
         D.ncx = sl.ncx;
+        D.cspan = sl.cspan;
         D.bond_off = (int)bij.size();
         D.n_bonds = S.n_bonds;
         for (int b = 0; b < S.n_bonds; ++b) {
@@ -609,6 +666,8 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         D.theta_stats = S.theta_stats;
         D.shared_freq = S.shared_freq > 0 ? S.shared_freq : 1;
         D.n_full = S.n_full;
+        D.w_first = w_glob;
+        D.w_count = sl.W;
         h->sys.push_back(D);
         const double sqc = std::sqrt(std::max(0.0, S.coul));
         for (int i = 0; i < S.n_atoms; ++i) {
@@ -745,6 +804,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
     HostView &hv = h->hv;
     hv.n_walkers = L.W;
     hv.n_sm = h->n_sm;
+    hv.ncs = L.ncs;
     hv.slot_off = h->slot_off.data();
     hv.slot_cap = h->slot_cap.data();
     hv.sc_cap = h->sc_cap.data();
@@ -761,6 +821,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
     *h->h_status = 0;
     CU(h, cudaEventCreateWithFlags(&h->status_ev, cudaEventDisableTiming));
     CU(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CU(h, cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
 
     rc = prime(h, 0, L.W, true, false, s);
     if (rc != LA_OK) return rc;
@@ -773,49 +834,59 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         char key[256];
         snprintf(key, sizeof key, "dev%d-sm%d-W%d-slots%lld-ent%d", dev, h->n_sm, L.W, L.slots, L.ent_cap);
         auto it = tune_cache().find(key);
-        int best_c = 4, best_k = L.chunk;
+        int best_c = 4, best_k = L.chunk, best_m = 3;
         if (it != tune_cache().end()) {
-            best_c = it->second.first;
-            best_k = it->second.second;
+            best_c = it->second[0];
+            best_k = it->second[1];
+            best_m = it->second[2];
         } else {
             // timing advances the walkers: the initial state is re-loaded after
             float best = 1e30f;
             const int ctas[] = {2, 3, 4, 6, 8};
-            const int chunksz[] = {16, 32, 64};
-            for (int k : chunksz) {
-                if ((L.ent_cap + k - 1) / k * k < L.chunk) continue;
-                if (k < L.chunk) continue;  // item capacity was sized for L.chunk
-                d.chunk = k;
-                for (int c : ctas) {
-                    set_pair_blocks(h, c);
-                    rc = prime(h, 0, L.W, true, false, s);
-                    if (rc != LA_OK) return rc;
-                    float ms = 0.f;
-                    rc = time_steps(h, 2, s, &ms);  // warm
-                    if (rc != LA_OK) return rc;
-                    rc = time_steps(h, 6, s, &ms);
-                    if (rc != LA_OK) return rc;
-                    if (ms < best) {
-                        best = ms;
-                        best_c = c;
-                        best_k = k;
+            const int chunksz[] = {32, 64};  // item capacity was sized for L.chunk = 32
+            const int minbs[] = {3, 4};
+            for (int m : minbs) {
+                h->hv.pair_minb = m;
+                for (int k : chunksz) {
+                    if (k < L.chunk) continue;
+                    d.chunk = k;
+                    for (int c : ctas) {
+                        set_pair_blocks(h, c);
+                        rc = prime(h, 0, L.W, true, false, s);
+                        if (rc != LA_OK) return rc;
+                        float ms = 0.f;
+                        rc = time_steps(h, 2, s, &ms);  // warm
+                        if (rc != LA_OK) return rc;
+                        rc = time_steps(h, 6, s, &ms);
+                        if (rc != LA_OK) return rc;
+                        if (ms < best) {
+                            best = ms;
+                            best_c = c;
+                            best_k = k;
+                            best_m = m;
+                        }
                     }
                 }
             }
-            tune_cache()[key] = {best_c, best_k};
+            tune_cache()[key] = {best_c, best_k, best_m};
         }
         d.chunk = best_k;
+        h->hv.pair_minb = best_m;
         set_pair_blocks(h, best_c);
         rc = upload();
         if (rc != LA_OK) return rc;
         h->steps = 0;
         rc = prime(h, 0, L.W, true, false, s);
         if (rc != LA_OK) return rc;
-        snprintf(rep, sizeof rep, "autotuned: pair CTAs/SM=%d, entries/item=%d, warps/CTA=8, graph steps=%d",
-                 best_c, best_k, h->graph_steps);
+        snprintf(rep, sizeof rep,
+                 "autotuned: pair CTAs/SM=%d, entries/item=%d, registers sized for %d CTAs/SM, warps/CTA=8, "
+                 "graph steps=%d",
+                 best_c, best_k, best_m, h->graph_steps);
     } else {
-        snprintf(rep, sizeof rep, "default: pair CTAs/SM=%d, entries/item=%d, warps/CTA=8, graph steps=%d",
-                 h->hv.pair_blocks / h->n_sm, d.chunk, h->graph_steps);
+        snprintf(rep, sizeof rep,
+                 "default: pair CTAs/SM=%d, entries/item=%d, registers sized for %d CTAs/SM, warps/CTA=8, "
+                 "graph steps=%d",
+                 h->hv.pair_blocks / h->n_sm, d.chunk, h->hv.pair_minb, h->graph_steps);
     }
     h->report = rep;
     rc = capture_graph(h);
@@ -836,7 +907,7 @@ int la_step_walkers(la_handle *h, int64_t n_steps, void *stream) {
     launch_finish(h->d, h->hv, 0, h->L.W, s);
     CU(h, cudaGetLastError());
     h->steps += n_steps;
-    h->launches += n_steps * h->launches_per_step + 1;
+    h->launches += reps * h->graph_steps * h->graph_launches_per_step + rem * h->launches_per_step + 1;
     post_status(h, s);
     return LA_OK;
 }
@@ -849,8 +920,10 @@ int la_step_walkers_plain(la_handle *h, int64_t n_steps, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const int W = h->L.W;
     for (int64_t k = 0; k < n_steps; ++k) {
+        // every walker's integrator runs before any rebuild: a walker that
+        // moves too far flags all walkers of its system for this step
+        for (int w = 0; w < W; ++w) launch_integrate(h->d, h->hv, w, w + 1, s);
         for (int w = 0; w < W; ++w) {
-            launch_integrate(h->d, h->hv, w, w + 1, s);
             launch_rebuild(h->d, h->hv, w, w + 1, s);
             launch_pairs(h->d, h->hv, w, w + 1, false, s);
             launch_bonded(h->d, h->hv, w, w + 1, false, s);
@@ -1051,23 +1124,21 @@ int la_get_pairs(la_handle *h, int walker, int32_t *pairs, uint8_t *kind, int64_
     CU(h, cudaMemcpy(&nsc, h->d.n_sc + walker, sizeof(int), cudaMemcpyDeviceToHost));
     CU(h, cudaMemcpy(nent.data(), h->d.sc_nent + W.sc_off, sizeof(int) * W.sc_cap, cudaMemcpyDeviceToHost));
     std::vector<int2> hdr((size_t)W.sc_cap * h->L.ent_cap);
-    std::vector<uint4> msk(2 * hdr.size());
+    std::vector<unsigned char> lbs(32 * hdr.size());
     CU(h, cudaMemcpy(hdr.data(), h->d.ent_hdr + (size_t)W.sc_off * h->L.ent_cap, sizeof(int2) * hdr.size(),
                      cudaMemcpyDeviceToHost));
-    CU(h, cudaMemcpy(msk.data(), h->d.ent_mask + 2 * (size_t)W.sc_off * h->L.ent_cap, sizeof(uint4) * msk.size(),
+    CU(h, cudaMemcpy(lbs.data(), h->d.ent_lb + 32 * (size_t)W.sc_off * h->L.ent_cap, lbs.size(),
                      cudaMemcpyDeviceToHost));
     std::vector<std::pair<long long, int>> out;
     for (int sl = 0; sl < nsc; ++sl) {
         for (int e = 0; e < nent[W.sc_off + sl - W.sc_off]; ++e) {
             const size_t ge = (size_t)sl * h->L.ent_cap + e;
             const int jbase = hdr[ge].x - W.slot_off;
-            const unsigned imask = (unsigned)hdr[ge].y >> 8;
-            const unsigned m[8] = {msk[2 * ge].x, msk[2 * ge].y, msk[2 * ge].z, msk[2 * ge].w,
-                                   msk[2 * ge + 1].x, msk[2 * ge + 1].y, msk[2 * ge + 1].z, msk[2 * ge + 1].w};
+            const unsigned imask = ((unsigned)hdr[ge].y >> 8) & 0xffu;
             for (int ic = 0; ic < NIC; ++ic) {
                 if (!(imask & (1u << ic))) continue;
                 for (int lane = 0; lane < 32; ++lane) {
-                    if (!(m[ic] & (1u << lane))) continue;
+                    if (!(lbs[32 * ge + lane] & (1u << ic))) continue;
                     const int a = aos[sl * SC + ic * IC + (lane & 7)], b = aos[jbase + (lane >> 3)];
                     const int i = std::min(a, b), j = std::max(a, b);
                     out.push_back({(long long)i * S.n_atoms + j, 0});
@@ -1132,17 +1203,27 @@ int la_stats(la_handle *h, int64_t *out, void *stream) {
     CU(h, cudaMemcpyAsync(nent.data(), h->d.sc_nent, sizeof(int) * nent.size(), cudaMemcpyDeviceToHost, s));
     CU(h, cudaMemcpyAsync(nsc.data(), h->d.n_sc, sizeof(int) * nsc.size(), cudaMemcpyDeviceToHost, s));
     CU(h, cudaStreamSynchronize(s));
-    long long ents = 0;
+    long long ents = 0, tiles = 0;
+    std::vector<int2> hdr(h->L.ent_cap);
     for (int w = 0; w < h->L.W; ++w)
-        for (int k = 0; k < nsc[w]; ++k) ents += nent[h->walk[w].sc_off + k];
+        for (int k = 0; k < nsc[w]; ++k) {
+            const int sc = h->walk[w].sc_off + k;
+            const int ne = nent[sc];
+            ents += ne;
+            if (ne <= 0) continue;
+            CU(h, cudaMemcpy(hdr.data(), h->d.ent_hdr + (size_t)sc * h->L.ent_cap, sizeof(int2) * ne,
+                             cudaMemcpyDeviceToHost));
+            for (int e = 0; e < ne; ++e) tiles += __builtin_popcount(((unsigned)hdr[e].y >> 8) & 0xffu);
+        }
     if (out) {
         out[0] = h->steps;
         out[1] = (int64_t)c[0];
-        out[2] = h->launches;
+        // list kernels run inside the graph only on rebuild steps (counted by the gate)
+        out[2] = h->launches + (int64_t)c[6] * rebuild_kernel_count(h->hv, 0, h->L.W);
         out[3] = (int64_t)c[1];
         out[4] = (int64_t)c[2];
         out[5] = ents;
-        out[6] = -1;  // listed atom pairs: see la_get_pairs
+        out[6] = tiles;
     }
     return LA_OK;
 }
@@ -1204,6 +1285,7 @@ int la_destroy(la_handle *h) {
     if (!h) return LA_OK;
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
     if (h->status_ev) cudaEventDestroy(h->status_ev);
     if (h->h_status) cudaFreeHost(h->h_status);
     delete h;

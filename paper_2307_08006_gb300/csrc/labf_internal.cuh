@@ -40,6 +40,7 @@ constexpr float FIX_LIMIT = 1073741824.0f;           // 2^30: |F| beyond risks i
 struct SysDev {
     int n_atoms, atom_off;        // atoms; offset into per-system atom arrays
     int n_alch, alch_off;         // alchemical atoms; offset into alch_atoms
+    int w_first, w_count;         // the system's walkers (consecutive)
     int P;                        // theta parameters: 3 n_alch + 1
     double box, box_inv;
     float boxf, box_invf;
@@ -53,6 +54,7 @@ struct SysDev {
     long long R;                  // integer list threshold
     int Rq;                       // list radius in quantized units (rounded up)
     int ncx;                      // columns per dimension
+    int cspan;                    // candidate columns per dimension around a super-cluster
     int bond_off, n_bonds, angle_off, n_angles, posres_off, n_posres;
     float posres_k;
     int fb_off, n_fb_a, n_fb_b;
@@ -114,6 +116,8 @@ struct Dev {
     int *atom_of_slot, *slot_walker;
     unsigned long long *F;
     int4 *uq;
+    int2 *smeta;                  // per slot: (exclusion group, alchemical flag)
+    int4 *sexcl;                  // per slot: extra excluded partners (atom ids)
     // rebuild scratch
     float4 *t_xq, *t_vv;
     int *t_old;
@@ -127,8 +131,14 @@ struct Dev {
     int *sc_member, *sc_n;
     int4 *bb_sc, *bb_ic, *bb_jc;  // (lo, hi) pairs; lo.w = real count
     int *sc_nent;
-    int2 *ent_hdr;                // (j-cluster base global slot, shift | imask << 8)
-    uint4 *ent_mask;              // 2 per entry
+    int2 *ent_hdr;                // (j-cluster base global slot, shift bits | imask << 8)
+    unsigned char *ent_lb;        // 32 per entry: lane l's bit ic = pair (8 ic + (l & 7), l >> 3)
+    // per (super-cluster, candidate column) sub-lists written by the list
+    // builder and compacted into ent_* in a fixed order
+    int ncs, sub_cap;
+    int2 *sub_hdr;
+    unsigned char *sub_lb;
+    int *sub_n;
     int4 *items;                  // (global sc, e0, e1, walker)
     int *n_items;
     // alchemical lists and partial sums
@@ -156,17 +166,39 @@ struct Dev {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_status(const Dev &d, unsigned bits) { atomicOr(d.status, bits); }
 
+// round(f * 2^32) as a two's-complement int64, computed from the IEEE-754
+// bits with 32/64-bit integer ALU operations only (a float -> int64
+// conversion instruction would run on the FP64 pipe, which is narrow on this
+// GPU).  f = 1.m * 2^(e-127), so f * 2^32 = M * 2^(e-118) with M = 1.m * 2^23.
+// Halves round away from zero; |f| must stay below 2^30 (the fixed-point
+// range); zeros and denormals give 0.
+__device__ __forceinline__ unsigned long long f2fix(float f) {
+    const unsigned b = __float_as_uint(f);
+    const int e = (int)((b >> 23) & 0xffu);
+    const unsigned long long M = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+    const int sh = e - 118;
+    unsigned long long v;
+    if (sh >= 0) v = M << (sh < 39 ? sh : 39);
+    else if (sh > -25) v = (M + (1ull << (-sh - 1))) >> (-sh);
+    else v = 0ull;
+    return (b >> 31) ? (unsigned long long)(-(long long)v) : v;
+}
+
 // Fixed-point force accumulation (2^32 units per force unit).  Integer adds
 // commute, so the sum is independent of the order of the atomics.
 __device__ __forceinline__ void add_force(const Dev &d, int slot, float fx, float fy, float fz) {
     unsigned long long *p = d.F + 3 * (size_t)slot;
-    atomicAdd(p + 0, (unsigned long long)__float2ll_rn(fx * F_TO_FIX));
-    atomicAdd(p + 1, (unsigned long long)__float2ll_rn(fy * F_TO_FIX));
-    atomicAdd(p + 2, (unsigned long long)__float2ll_rn(fz * F_TO_FIX));
+    atomicAdd(p + 0, f2fix(fx));
+    atomicAdd(p + 1, f2fix(fy));
+    atomicAdd(p + 2, f2fix(fz));
 }
 
+// fixed point back to float from its two 32-bit halves (no 64-bit
+// conversion instruction): hi + lo 2^-32, within 1 ulp of the exact value
 __device__ __forceinline__ float fix_to_float(unsigned long long v) {
-    return __ll2float_rn((long long)v) * FIX_TO_F;
+    const int hi = (int)(v >> 32);
+    const unsigned lo = (unsigned)(v & 0xffffffffull);
+    return fmaf((float)lo, FIX_TO_F, (float)hi);
 }
 
 __device__ __forceinline__ float min_image(float dx, float L, float Linv) {

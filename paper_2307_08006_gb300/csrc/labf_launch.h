@@ -11,7 +11,7 @@ namespace labf {
 
 // Host copies of the per-walker offsets the launchers size grids with.
 struct HostView {
-    int n_walkers = 0, n_sm = 0, pair_blocks = 0;
+    int n_walkers = 0, n_sm = 0, pair_blocks = 0, ncs = 1, pair_minb = 3;
     const int *slot_off = nullptr, *slot_cap = nullptr, *sc_cap = nullptr, *n_cols = nullptr;
     const int *alch_base = nullptr, *n_alch = nullptr, *item_cap = nullptr;
     const int *bo_off = nullptr, *n_bo = nullptr;
@@ -20,6 +20,7 @@ struct HostView {
 void launch_integrate(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
 void launch_finish(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
 void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
+void launch_gate(const Dev &d, int w0, int w1, cudaGraphConditionalHandle handle, cudaStream_t s);
 int rebuild_kernel_count(const HostView &hv, int w0, int w1);
 void launch_pairs(const Dev &d, const HostView &hv, int w0, int w1, bool energy, cudaStream_t s);
 void launch_bonded(const Dev &d, const HostView &hv, int w0, int w1, bool energy, cudaStream_t s);
