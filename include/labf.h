@@ -234,10 +234,16 @@ int la_set_alch_params(la_handle *h, int sys, const double *theta, void *stream)
 /*
  * la_read_theta: per-bin theta statistics of stage `stage` of system `sys`
  * (theta_stats = 1): sums of d2U/dlambda dtheta, of dU/dtheta and of
- * dU/dlambda * dU/dtheta, each host [n_bins][P].  Synchronising.
+ * dU/dlambda * dU/dtheta, each host [n_bins][P] (may be NULL), and the
+ * derivative of the stage's Delta A with respect to theta (host [P], may be
+ * NULL): sum_k w [<d2U/dlambda dtheta>_k - Cov_k(dU/dlambda, dU/dtheta)/kT].
+ * The paper does not differentiate Delta A; the covariance term is needed
+ * because the lambda-conditional ensemble itself depends on theta.  All
+ * samples folded so far count (merged or not).  Synchronising.  Returns
+ * LA_WARN_EMPTY_BIN (NaN derivatives) when a bin is empty.
  */
 int la_read_theta(la_handle *h, int sys, int stage, double *sum_d2, double *sum_d, double *sum_sd,
-                  void *stream);
+                  double *dA_dtheta, void *stream);
 
 /*
  * la_get_pairs: expand the current neighbour list of one walker into atom

@@ -116,6 +116,7 @@ def _declare(lib):
     lib.or_pair_set.argtypes = [C.POINTER(_System), P, C.c_double, C.c_int64, P, P, C.c_int64]
     lib.or_pair_set.restype = C.c_int64
     lib.or_energy_forces.argtypes = [C.POINTER(_System), P, C.c_double, P, P, P, P, P, P]
+    lib.or_energy_forces_masked.argtypes = [C.POINTER(_System), P, C.c_double, P, P, P, P, P, P, P]
     lib.or_set_threads.argtypes = [C.c_int]
     lib.or_get_max_threads.restype = C.c_int
     lib.or_bin.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
@@ -241,6 +242,25 @@ def energy_forces(osys: OracleSystem, x: np.ndarray, lam: float) -> dict:
                              _ptr(dUdl), _ptr(dth), _ptr(d2th))
     return dict(terms=terms, U=float(terms.sum()), F=F, dl=dl, dUdl=float(dUdl[0]), dth=dth,
                 d2th=d2th)
+
+
+def energy_forces_masked(osys: OracleSystem, x: np.ndarray, lam: float, atoms) -> dict:
+    """Forces on `atoms` and dU/dlambda (complete); other forces and the
+    energy terms are partial.  Visits only pairs touching a selected or an
+    alchemical atom."""
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    n = osys.spec.n
+    mask = np.zeros(n, np.uint8)
+    mask[np.asarray(atoms)] = 1
+    terms = np.zeros(N_TERMS)
+    F = np.zeros((n, 3))
+    dl = np.zeros(3)
+    dUdl = np.zeros(1)
+    P = osys.n_theta
+    dth, d2th = np.zeros(P), np.zeros(P)
+    _load().or_energy_forces_masked(C.byref(osys.c), _ptr(x), float(lam), _ptr(mask), _ptr(terms), _ptr(F),
+                                    _ptr(dl), _ptr(dUdl), _ptr(dth), _ptr(d2th))
+    return dict(F=F, dl=dl, dUdl=float(dUdl[0]), dth=dth, d2th=d2th)
 
 
 def set_threads(n: int) -> None:

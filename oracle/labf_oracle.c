@@ -223,9 +223,29 @@ static void rf_constants(double rc, double eps_rf, double *krf, double *crf) {
  * dl = {dU/dlambda_v, dU/dlambda_e, dU/dlambda from terms that use lambda itself};
  * dth / d2th: [P] dU/dtheta and d2U/dlambda dtheta, theta = (eps_a, sigma_a, q_a)
  * for each alchemical atom a in index order, then k1. */
+static void energy_forces_impl(const or_system *sys, const double *x, double lam,
+                               double terms[OR_N_TERMS], double *F, double dl[3], double *dUdl,
+                               double *dth, double *d2th, const uint8_t *mask);
+
 void or_energy_forces(const or_system *sys, const double *x, double lam,
                       double terms[OR_N_TERMS], double *F, double dl[3], double *dUdl,
                       double *dth, double *d2th) {
+    energy_forces_impl(sys, x, lam, terms, F, dl, dUdl, dth, d2th, NULL);
+}
+
+/* Same, but nonbonded pairs are visited only when one atom is selected by
+ * mask or alchemical: the forces on selected atoms, dU/dlambda and the theta
+ * derivatives are complete; the other forces and the energy terms are not.
+ * For sampled checks of systems too large for the full O(N^2) pass. */
+void or_energy_forces_masked(const or_system *sys, const double *x, double lam, const uint8_t *mask,
+                             double terms[OR_N_TERMS], double *F, double dl[3], double *dUdl,
+                             double *dth, double *d2th) {
+    energy_forces_impl(sys, x, lam, terms, F, dl, dUdl, dth, d2th, mask);
+}
+
+static void energy_forces_impl(const or_system *sys, const double *x, double lam,
+                               double terms[OR_N_TERMS], double *F, double dl[3], double *dUdl,
+                               double *dth, double *d2th, const uint8_t *mask) {
     const int n = sys->n;
     const double L = sys->box;
     double path[4];
@@ -252,6 +272,7 @@ void or_energy_forces(const or_system *sys, const double *x, double lam,
     /* ---- nonbonded pairs, O(N^2) with the minimum image ---- */
     for (int i = 0; i < n; ++i) {
         for (int j = i + 1; j < n; ++j) {
+            if (mask && !mask[i] && !mask[j] && !sys->alch[i] && !sys->alch[j]) continue;
             if (or_excluded(sys, i, j)) continue;
             double d[3];
             for (int c = 0; c < 3; ++c) d[c] = min_image(x[3 * i + c] - x[3 * j + c], L);

@@ -95,6 +95,10 @@ void or_energy_forces(const or_system *sys, const double *x, double lam,
                       double terms[OR_N_TERMS], double *F, double dl[3], double *dUdl,
                       double *dth, double *d2th);
 
+void or_energy_forces_masked(const or_system *sys, const double *x, double lam, const uint8_t *mask,
+                             double terms[OR_N_TERMS], double *F, double dl[3], double *dUdl,
+                             double *dth, double *d2th);
+
 void or_set_threads(int n);
 int or_get_max_threads(void);
 

@@ -1088,25 +1088,61 @@ int la_set_alch_params(la_handle *h, int sys, const double *theta, void *stream)
     return sync_status(h, s, nullptr);
 }
 
-int la_read_theta(la_handle *h, int sys, int stage, double *sum_d2, double *sum_d, double *sum_sd, void *stream) {
+int la_read_theta(la_handle *h, int sys, int stage, double *sum_d2, double *sum_d, double *sum_sd,
+                  double *dA_dtheta, void *stream) {
     if (!h) return LA_ERR_INVALID_ARG;
     if (sys < 0 || sys >= (int)h->sys.size() || stage < 0 || stage >= h->sys_nstage[sys])
         return fail(h, LA_ERR_INVALID_ARG, "bad system/stage");
     cudaStream_t s = (cudaStream_t)stream;
     const StageDev &st = h->stages[h->sys_stage0[sys] + stage];
-    const int P = h->sys[sys].P, PM = h->L.P_max;
-    std::vector<double> buf((size_t)st.n_bins * PM);
-    double *outs[3] = {sum_d2, sum_d, sum_sd};
+    const int P = h->sys[sys].P, PM = h->L.P_max, nb = st.n_bins, MB = h->L.max_bins;
+    std::vector<double> th[3];
     double *srcs[3] = {h->d.th_d2, h->d.th_d, h->d.th_sd};
     for (int q = 0; q < 3; ++q) {
-        if (!outs[q]) continue;
-        CU(h, cudaMemcpyAsync(buf.data(), srcs[q] + (size_t)st.bin_off * PM, sizeof(double) * buf.size(),
+        th[q].resize((size_t)nb * PM);
+        CU(h, cudaMemcpyAsync(th[q].data(), srcs[q] + (size_t)st.bin_off * PM, sizeof(double) * th[q].size(),
                               cudaMemcpyDeviceToHost, s));
-        CU(h, cudaStreamSynchronize(s));
-        for (int k = 0; k < st.n_bins; ++k)
-            for (int p = 0; p < P; ++p) outs[q][(size_t)k * P + p] = buf[(size_t)k * PM + p];
     }
-    return LA_OK;
+    // samples per bin (merged and walker-local) and their dU/dlambda sums
+    std::vector<double> s1(nb), l1((size_t)h->L.W * MB);
+    std::vector<unsigned long long> c(nb), lc((size_t)h->L.W * MB);
+    CU(h, cudaMemcpyAsync(s1.data(), h->d.abf_sum + st.bin_off, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(c.data(), h->d.abf_count + st.bin_off, sizeof(unsigned long long) * nb,
+                          cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(l1.data(), h->d.dl_sum, sizeof(double) * l1.size(), cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(lc.data(), h->d.dl_count, sizeof(unsigned long long) * lc.size(), cudaMemcpyDeviceToHost, s));
+    int rc = sync_status(h, s, nullptr);
+    if (rc != LA_OK) return rc;
+    double *outs[3] = {sum_d2, sum_d, sum_sd};
+    for (int q = 0; q < 3; ++q)
+        if (outs[q])
+            for (int k = 0; k < nb; ++k)
+                for (int p = 0; p < P; ++p) outs[q][(size_t)k * P + p] = th[q][(size_t)k * PM + p];
+    if (dA_dtheta) {
+        // d Delta A / d theta = sum_k w [<d2U/dl dth> - beta Cov(dU/dl, dU/dth)]
+        // (the lambda-conditional ensemble depends on theta, hence the covariance)
+        const double beta = 1.0 / h->sys[sys].kT;
+        for (int p = 0; p < P; ++p) dA_dtheta[p] = 0.0;
+        for (int k = 0; k < nb; ++k) {
+            double sum = s1[k], cnt = (double)c[k];
+            for (int w = st.w0; w < st.w1; ++w) {
+                sum += l1[(size_t)w * MB + k];
+                cnt += (double)lc[(size_t)w * MB + k];
+            }
+            if (cnt <= 0.0) {
+                for (int p = 0; p < P; ++p) dA_dtheta[p] = std::nan("");
+                rc = LA_WARN_EMPTY_BIN;
+                continue;
+            }
+            const double ms = sum / cnt;
+            for (int p = 0; p < P; ++p) {
+                const double m2 = th[0][(size_t)k * PM + p] / cnt, md = th[1][(size_t)k * PM + p] / cnt;
+                const double msd = th[2][(size_t)k * PM + p] / cnt;
+                dA_dtheta[p] += st.width * (m2 - beta * (msd - ms * md));
+            }
+        }
+    }
+    return rc;
 }
 
 int la_get_pairs(la_handle *h, int walker, int32_t *pairs, uint8_t *kind, int64_t cap, int64_t *count,

@@ -105,7 +105,7 @@ def load(build_if_missing: bool = False):
     lib.la_get_state.argtypes = [H, I, P, P, P, P, P, P]
     lib.la_set_state.argtypes = [H, I, P, P, P, P, P]
     lib.la_set_alch_params.argtypes = [H, I, P, P]
-    lib.la_read_theta.argtypes = [H, I, I, P, P, P, P]
+    lib.la_read_theta.argtypes = [H, I, I, P, P, P, P, P]
     lib.la_get_pairs.argtypes = [H, I, P, P, C.c_int64, P, P]
     lib.la_lambda_path.argtypes = [H, P, I, D, D, P, P]
     lib.la_sync.argtypes = [H, P, P]
@@ -335,8 +335,10 @@ class Engine:
         nb = self.systems[sys].run.stages[stage].n_bins
         P = 3 * spec.n_alch + 1
         a, b, c = np.zeros((nb, P)), np.zeros((nb, P)), np.zeros((nb, P))
-        self._check(self.lib.la_read_theta(self.handle, sys, stage, _p(a), _p(b), _p(c), self._stream(stream)))
-        return dict(sum_d2=a, sum_d=b, sum_sd=c)
+        g = np.zeros(P)
+        rc = self._check(self.lib.la_read_theta(self.handle, sys, stage, _p(a), _p(b), _p(c), _p(g),
+                                                self._stream(stream)))
+        return dict(sum_d2=a, sum_d=b, sum_sd=c, dA_dtheta=g, empty_bin=rc == LA_WARN_EMPTY_BIN)
 
     def get_pairs(self, walker: int, stream=None) -> Tuple[np.ndarray, np.ndarray]:
         cnt = C.c_int64(0)

@@ -310,7 +310,8 @@ def _serpentine(n_sites: int, lattice: float, dims: Tuple[int, int, int]) -> np.
 
 
 def large_complex(seed: int = 8010, n_waters: int = 31000, n_chain: int = 3000,
-                  n_lig: int = 40, r_cut: float = 1.2, density_atoms: float = 98.4) -> SystemSpec:
+                  n_lig: int = 40, r_cut: float = 1.2, density_atoms: float = 98.4,
+                  jitter: float = 0.005) -> SystemSpec:
     """31000 flexible waters, a 3000-site bonded chain held by positional
     restraints, and a 40-site alchemical ligand with a flat-bottom restraint
     between its centre of mass and that of the chain sites near it.  The box
@@ -326,40 +327,17 @@ def large_complex(seed: int = 8010, n_waters: int = 31000, n_chain: int = 3000,
     lig += np.array([box / 2 - 0.45, box / 2 - 0.3, box / 2 + 1.95])
     solid = np.concatenate([chain, lig])
     # water grid: finest cubic grid whose free sites cover n_waters
+    from scipy.spatial import cKDTree
+
+    tree = cKDTree(solid % box, boxsize=box)
     per_side = int(np.ceil((n_waters * 1.15) ** (1.0 / 3.0)))
     while True:
         spacing = box / per_side
         g = (np.stack(np.meshgrid(*[np.arange(per_side)] * 3, indexing="ij"), -1)
              .reshape(-1, 3) + 0.25) * spacing
-        # remove grid sites near chain or ligand sites (cell hashing by lattice)
-        keep = np.ones(len(g), bool)
-        cell = 0.35
-        nc = int(box // cell)
-        occ = {}
-        for p in solid:
-            key = tuple((p // cell).astype(int) % nc)
-            occ.setdefault(key, []).append(p)
-        for idx, p in enumerate(g):
-            c = (p // cell).astype(int)
-            near = False
-            for dx in (-1, 0, 1):
-                for dy in (-1, 0, 1):
-                    for dz in (-1, 0, 1):
-                        key = tuple((c + (dx, dy, dz)) % nc)
-                        for q in occ.get(key, ()):
-                            d = p - q
-                            d -= box * np.round(d / box)
-                            if d @ d < 0.33 ** 2:
-                                near = True
-                                break
-                        if near:
-                            break
-                    if near:
-                        break
-                if near:
-                    break
-            keep[idx] = not near
-        free = g[keep]
+        # drop grid sites within 0.33 nm of a chain or ligand site (periodic)
+        dist, _ = tree.query(g % box, k=1, distance_upper_bound=0.33)
+        free = g[~np.isfinite(dist)]
         if len(free) >= n_waters:
             break
         per_side += 1
@@ -367,7 +345,10 @@ def large_complex(seed: int = 8010, n_waters: int = 31000, n_chain: int = 3000,
     sites = free[pick]
     xw = np.concatenate([_water_molecule(o) for o in sites])
     nw = 3 * n_waters
-    x = np.concatenate([xw, chain, lig]) % box
+    x = np.concatenate([xw, chain, lig])
+    # seeded jitter: lattice starts put many pair distances exactly on the
+    # cutoff (1.2 nm = 8 x 0.15 nm), where any rounding flips the pair
+    x = (x + rng.uniform(-jitter, jitter, x.shape)) % box
     n = x.shape[0]
     mass = np.empty(n)
     charge = np.empty(n)

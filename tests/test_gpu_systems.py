@@ -1,0 +1,233 @@
+"""GPU tests of the workload shapes beyond the single small box: the uneven
+batch (8 systems, 64 walkers in one engine), differentiation (autograd
+through the engine at 21 lambda values), the large restrained complex
+(sampled forces), statistical free-energy parity, and error paths.
+
+Oracle values come from oracle/ only (FP64, O(N^2) or masked O(k N)).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_08006_gb300 import labf, synth
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-5
+
+
+def rel_rms(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
+
+
+def jittered(sp, seed, amp=0.01):
+    rng = np.random.default_rng(seed)
+    sp.x = ((sp.x + rng.normal(0.0, amp, sp.x.shape)) % sp.box).astype(np.float32)
+    return sp
+
+
+def sample_atoms(spec, k, seed, extra=()):
+    rng = np.random.default_rng(seed)
+    idx = set(rng.choice(spec.n, k, replace=False).tolist()) | set(int(i) for i in extra)
+    return np.asarray(sorted(idx))
+
+
+def check_sampled(eng, walker, spec, x, lam, atoms):
+    g = eng.energy_forces(walker)
+    ref = oracle.energy_forces_masked(oracle.OracleSystem(spec), x.astype(np.float64), lam, atoms)
+    f = g["F"].cpu().numpy().astype(np.float64)[atoms]
+    fr = ref["F"][atoms]
+    assert rel_rms(f, fr) < FORCE_TOL
+    scale = max(1.0, abs(ref["dl"][0]) + abs(ref["dl"][1]) + abs(ref["dl"][2]))
+    assert abs(g["dUdl"] - ref["dUdl"]) <= FORCE_TOL * scale
+    return g, ref
+
+
+# ---------------------------------------------------------------------------
+# uneven batch: 8 water boxes (256 ... 8192 waters), 8 walkers each
+# ---------------------------------------------------------------------------
+def _uneven_inputs(n_walkers_per_system=8, seed=8008):
+    systems = synth.uneven_batch(seed)
+    inputs = []
+    for k, sp in enumerate(systems):
+        jittered(sp, seed + k)
+        run = synth.uneven_run(seed=seed + k, walkers_per_system=n_walkers_per_system)
+        lam0 = list(np.linspace(0.05, 0.45, run.stages[0].n_walkers)) + \
+            list(np.linspace(0.55, 0.95, run.stages[1].n_walkers))
+        inputs.append(labf.SystemInput(sp, run, synth.initial_state(sp, run, lam0=lam0)))
+    return inputs
+
+
+def test_uneven_batch_forces_pairs_and_forms():
+    inputs = _uneven_inputs()
+    eng = labf.Engine(inputs)
+    assert eng.n_walkers == 64
+    w = 0
+    for k, si in enumerate(inputs):
+        atoms = sample_atoms(si.spec, 48, 100 + k, extra=np.nonzero(si.spec.alch)[0])
+        for wl in (0, si.run.n_walkers - 1):
+            check_sampled(eng, w + wl, si.spec, si.state.x[wl], si.state.lam[wl], atoms)
+        w += si.run.n_walkers
+    # pair set of the smallest box (r_c = 0.85 nm, several images per cluster pair)
+    sp0 = inputs[0].spec
+    pairs, kind = eng.get_pairs(0)
+    opairs, okind = oracle.pair_set(oracle.OracleSystem(sp0), inputs[0].state.x[0],
+                                    sp0.r_cut + inputs[0].run.skin)
+    assert np.array_equal(pairs, opairs) and np.array_equal(kind, okind)
+    # batched (graph) and plain forms agree bit for bit on the uneven batch
+    e2 = labf.Engine(inputs)
+    eng.step(25)
+    e2.step_plain(25)
+    for ww in (0, 9, 31, 63):
+        a, b = eng.get_state(ww), e2.get_state(ww)
+        assert np.array_equal(a["x"], b["x"]) and a["lam"] == b["lam"]
+
+
+# ---------------------------------------------------------------------------
+# differentiation: U(x, lambda, theta) through torch.autograd at 21 lambdas
+# ---------------------------------------------------------------------------
+def test_autograd_gradients_match_oracle_at_21_lambdas():
+    import torch
+
+    from paper_2307_08006_gb300 import autograd
+
+    sp = jittered(synth.water_box(4096, 12, seed=8009), 8009)
+    run = synth.water_run(seed=8009, walkers_per_stage=1)
+    run.stages = [synth.Stage(0.0, 1.0, 20, 1)]
+    state = synth.initial_state(sp, run, lam0=[0.0])
+    eng = labf.engine_for(sp, run, state)
+    dev = torch.device("cuda", 0)
+    osys = oracle.OracleSystem(sp)
+    atoms = sample_atoms(sp, 64, 7, extra=np.nonzero(sp.alch)[0])
+    theta0 = autograd.theta_of(sp)
+    n_alch = theta0.shape[0]
+    for lam in np.linspace(0.0, 1.0, 21):
+        x = torch.tensor(state.x[0], device=dev, requires_grad=True)
+        lt = torch.tensor(lam, dtype=torch.float64, requires_grad=True)
+        th = torch.tensor(theta0, dtype=torch.float64, device=dev, requires_grad=True)
+        U = autograd.energy(eng, 0, x, lt, th)
+        gx, gl, gth = torch.autograd.grad(U, [x, lt, th])
+        ref = oracle.energy_forces_masked(osys, state.x[0].astype(np.float64), lam, atoms)
+        fx = -gx.cpu().numpy().astype(np.float64)[atoms]
+        assert rel_rms(fx, ref["F"][atoms]) < FORCE_TOL
+        dscale = max(1.0, abs(ref["dl"][0]) + abs(ref["dl"][1]) + abs(ref["dl"][2]))
+        assert abs(float(gl) - ref["dUdl"]) <= FORCE_TOL * dscale
+        rth = ref["dth"][:3 * n_alch].reshape(n_alch, 3)
+        tscale = max(1.0, float(np.abs(rth).max()))
+        np.testing.assert_allclose(gth.cpu().numpy(), rth, rtol=1e-4, atol=1e-5 * tscale)
+        # second derivatives d2U/dlambda dtheta from the same pass
+        g = eng.energy_forces(0)
+        r2 = ref["d2th"][:3 * n_alch]
+        np.testing.assert_allclose(g["d2th"][:3 * n_alch], r2, rtol=1e-4,
+                                   atol=1e-5 * max(1.0, float(np.abs(r2).max())))
+
+
+# ---------------------------------------------------------------------------
+# large restrained complex: 96k atoms, sampled forces (incl. restraints)
+# ---------------------------------------------------------------------------
+def test_large_complex_sampled_forces_and_steps():
+    sp = synth.large_complex()
+    run = synth.large_complex_run(walkers_per_stage=1)
+    state = synth.initial_state(sp, run, lam0=[0.3, 0.7])
+    eng = labf.engine_for(sp, run, state)
+    lig = np.nonzero(sp.alch)[0]
+    atoms = sample_atoms(sp, 40, 11, extra=list(lig[:8]) + list(sp.fb_b[:8]) + list(sp.posres_idx[:8]))
+    for w in range(2):
+        check_sampled(eng, w, sp, state.x[w], state.lam[w], atoms)
+    eng.step(40)
+    eng.sync()
+    s = eng.get_state(1)
+    check_sampled(eng, 1, sp, s["x"], s["lam"], atoms)
+
+
+# ---------------------------------------------------------------------------
+# free energy: closed form on the GPU, and GPU vs oracle statistics
+# ---------------------------------------------------------------------------
+@pytest.mark.slow
+def test_harmonic_switch_free_energy_and_theta_gradient_on_gpu():
+    """Delta A = (kT/2) ln(k1/k0) within 0.05 kT and d Delta A / d k1 =
+    kT / (2 k1) from the GPU accumulator (1-D well, 4 walkers, 3 seeds)."""
+    vals, grads = [], []
+    for seed in range(3):
+        sp = synth.harmonic_well(dims=1, k0=1.0, k1=4.0)
+        run = synth.harmonic_run(seed=300 + seed, n_walkers=4)
+        run.theta_stats = True
+        eng = labf.engine_for(sp, run)
+        eng.step(250_000)
+        a = eng.read_abf(0, 0)
+        assert not a["empty_bin"]
+        vals.append(a["dA"])
+        grads.append(eng.read_theta(0, 0)["dA_dtheta"][-1])
+    assert np.mean(vals) == pytest.approx(0.5 * np.log(4.0), abs=0.05)
+    assert np.mean(grads) == pytest.approx(1.0 / 8.0, abs=0.02)
+
+
+@pytest.mark.slow
+def test_lj_fluid_delta_a_gpu_vs_oracle_two_combined_se():
+    """Delta A of the LJ-fluid workload from GPU and oracle runs (8 seeds
+    each, 20 000 steps, 4 walkers) agree within two combined standard errors."""
+    oracle.set_threads(4)
+    res = {"gpu": [], "cpu": []}
+    for seed in range(8):
+        sp = synth.lj_fluid()
+        run = synth.lj_fluid_run(seed=500 + seed)
+        st = synth.initial_state(sp, run)
+        eng = labf.engine_for(sp, run, st)
+        eng.step(20_000)
+        a = eng.read_abf(0, 0)
+        assert not a["empty_bin"]
+        res["gpu"].append(a["dA"])
+        sim = oracle.Simulation(sp, run, st)
+        sim.run(20_000)
+        res["cpu"].append(sim.delta_a(0)[2])
+    g, c = np.asarray(res["gpu"]), np.asarray(res["cpu"])
+    se = np.sqrt(g.var(ddof=1) / len(g) + c.var(ddof=1) / len(c))
+    assert abs(g.mean() - c.mean()) <= 2.0 * se + 1e-9, (g.mean(), c.mean(), se)
+
+
+def test_shared_freq_merge_matches_oracle():
+    sp = jittered(synth.water_box(100, 6, seed=61, box=1.5, r_cut=0.6), 61)
+    run = synth.water_run(seed=62, walkers_per_stage=2, n_bins=10)
+    run.shared_freq = 4
+    st = synth.initial_state(sp, run, lam0=[0.1, 0.3, 0.6, 0.8])
+    eng = labf.engine_for(sp, run, st)
+    sim = oracle.Simulation(sp, run, st)
+    for n in (3, 5):
+        eng.step(n)
+        sim.run(n)
+        for stage in range(2):
+            a = eng.read_abf(0, stage)
+            s, _, c = sim.stage_bins(stage)
+            assert np.array_equal(a["count"], c)
+            np.testing.assert_allclose(a["sum"], s, rtol=1e-4, atol=1e-3 * max(1.0, np.abs(s).max()))
+
+
+# ---------------------------------------------------------------------------
+# error paths (no GPU fault: every write is bounds-checked, the status word
+# reports the condition)
+# ---------------------------------------------------------------------------
+def test_list_overflow_is_reported():
+    sp = jittered(synth.water_box(100, 6, seed=71, box=1.5, r_cut=0.6), 71)
+    # all atoms squeezed into a corner: capacities are sized for the box's
+    # average density, so the alchemical lists overflow at the first build
+    sp.x = (sp.x * 0.4).astype(np.float32)
+    run = synth.water_run(seed=72, walkers_per_stage=1, n_bins=10)
+    with pytest.raises(labf.LabfError) as ei:
+        labf.engine_for(sp, run, options=dict(list_capacity_factor=1.0))
+    assert ei.value.code in (-6, -7, -8)
+
+
+def test_nonfinite_state_is_reported():
+    sp = jittered(synth.water_box(100, 6, seed=81, box=1.5, r_cut=0.6), 81)
+    run = synth.water_run(seed=82, walkers_per_stage=1, n_bins=10)
+    eng = labf.engine_for(sp, run)
+    s = eng.get_state(0)
+    x = s["x"].copy()
+    x[5, 1] = np.nan
+    eng.set_state(0, x=x)
+    with pytest.raises(labf.LabfError) as ei:
+        eng.step(2)
+        eng.sync()
+    assert ei.value.code in (-7, -8, -9)
+    with pytest.raises(labf.LabfError):
+        eng.step(1)  # sticky

@@ -510,3 +510,18 @@ def test_abf_flattens_lambda_histogram():
     r_abf = counts[True].max() / counts[True].min()
     assert r_plain > 5.0
     assert r_abf < 2.0
+
+
+def test_masked_evaluation_matches_full():
+    """The masked pass visits only pairs touching selected or alchemical
+    atoms: forces on the selected atoms, dU/dlambda and the theta
+    derivatives equal those of the full pass."""
+    sp, x = _restrained_small(6)
+    o = oracle.OracleSystem(sp)
+    atoms = np.array([0, 4, 17, 30, sp.n - 2])
+    for lam in (0.2, 0.7):
+        full = oracle.energy_forces(o, x, lam)
+        part = oracle.energy_forces_masked(o, x, lam, atoms)
+        np.testing.assert_allclose(part["F"][atoms], full["F"][atoms], rtol=1e-12, atol=1e-10)
+        assert part["dUdl"] == pytest.approx(full["dUdl"], rel=1e-12, abs=1e-12)
+        np.testing.assert_allclose(part["dth"], full["dth"], rtol=1e-12, atol=1e-12)
