@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int 
         if (lane < 2 * NIC) s_bb[wib][lane] = d.bb_ic[2 * (size_t)s * NIC + lane];
         __syncwarp();
         const long long R = S.R;
-        const int U = 1 << 24, H = 1 << 23;
+        const int U = 1 << 24;
         const int ty = floordiv(cy, ncx), wy = cy - ty * ncx;
         const int tx = floordiv(cx, ncx), wx = cx - tx * ncx;
         const int col = wx + ncx * wy;
@@ -432,10 +432,16 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int 
                         const int2 mi = s_m[wib][si];
                         bool ok = ui.w >= 0 && uj.w >= 0 && !mi.y && !mj.y;
                         if (self0) ok = ok && si < jc * JC + jb;
+                        // D < R implies every component lies in (-2^23, 2^23) (R <= 2^46
+                        // because L >= 2 r_list), i.e. this shift is the minimum image
                         const int dx = uj.x + shx - ui.x, dy = uj.y + shy - ui.y, dz = uj.z + shz - ui.z;
-                        ok = ok && dx >= -H && dx < H && dy >= -H && dy < H && dz >= -H && dz < H;
-                        if (ok) ok = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz < R;
-                        if (ok) ok = !excluded_meta(ui.w, mi, s_e[wib][si], uj.w, mj, ej);
+                        ok = ok && (long long)dx * dx + (long long)dy * dy + (long long)dz * dz < R;
+                        if (ok) {
+                            const int4 ei = s_e[wib][si];
+                            if (mi.x >= 0 && mi.x == mj.x) ok = false;
+                            else if ((ei.x & ei.y & ei.z & ei.w & ej.x & ej.y & ej.z & ej.w) != -1)
+                                ok = !excluded_meta(ui.w, mi, ei, uj.w, mj, ej);  // some partner list is not empty
+                        }
                         if (ok) lbyte |= 1u << ic;
                         if (__any_sync(0xffffffffu, ok)) imask |= 1u << ic;
                     }

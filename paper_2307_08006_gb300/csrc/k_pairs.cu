@@ -30,16 +30,16 @@
 
 namespace labf {
 
-constexpr int PAIR_WARPS = 8;
 constexpr int EPC = 32;  // entries prepared per pass (one per lane)
 constexpr unsigned FULL = 0xffffffffu;
 
+template <int WARPS>
 struct PairShared {
-    float4 sxq[PAIR_WARPS][SC];      // the item's super-cluster
-    float2 slj[PAIR_WARPS][SC];
-    float4 jx[PAIR_WARPS][EPC][JC];  // prepared j-atoms (shift applied)
-    float2 jl[PAIR_WARPS][EPC][JC];
-    unsigned char lb[PAIR_WARPS][EPC][32];
+    float4 sxq[WARPS][SC];      // the item's super-cluster
+    float2 slj[WARPS][SC];
+    float4 jx[WARPS][EPC][JC];  // prepared j-atoms (shift applied)
+    float2 jl[WARPS][EPC][JC];
+    unsigned char lb[WARPS][EPC][32];
     int pre[LA_MAX_WALKERS_PER_LAUNCH + 1];
 };
 
@@ -47,8 +47,8 @@ struct PairShared {
 // more work; the last one resets both for the next launch
 constexpr int CTR_ITEM = 4, CTR_DONE = 5;
 
-template <bool ENERGY>
-__device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int nblk, PairShared &sh) {
+template <bool ENERGY, int WARPS>
+__device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int nblk, PairShared<WARPS> &sh) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int ia = lane & 7, jb = lane >> 3;
     const int nw = w1 - w0;
@@ -202,7 +202,7 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
     if (lane == 0) {
         __threadfence();
         const unsigned long long done = atomicAdd(&d.counters[CTR_DONE], 1ull);
-        if (done == (unsigned long long)nblk * PAIR_WARPS - 1ull) {
+        if (done == (unsigned long long)nblk * WARPS - 1ull) {
             d.counters[CTR_ITEM] = 0ull;
             d.counters[CTR_DONE] = 0ull;
             __threadfence();
@@ -210,11 +210,11 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
     }
 }
 
-template <bool ENERGY>
+template <bool ENERGY, int WARPS>
 __device__ __forceinline__ void alch_items(const Dev &d, int w0, int w1, int a0, int a1, int blk, int nblk) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nwarps = nblk * PAIR_WARPS;
-    for (int it = a0 + blk * PAIR_WARPS + wib; it < a1; it += nwarps) {
+    const int nwarps = nblk * WARPS;
+    for (int it = a0 + blk * WARPS + wib; it < a1; it += nwarps) {
         int lo = w0, hi = w1 - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
@@ -328,13 +328,14 @@ __device__ __forceinline__ void alch_items(const Dev &d, int w0, int w1, int a0,
     }
 }
 
-// MINB: resident CTAs per SM the register allocation is sized for (the
-// autotuner picks 3, spill-free, or 4, more warps to hide latency)
-template <bool ENERGY, int MINB>
-__global__ void __launch_bounds__(PAIR_WARPS * 32, MINB) k_pairs(Dev d, int w0, int w1, int nblk_pairs, int a0, int a1) {
-    __shared__ PairShared sh;
+// WARPS x 32 threads per CTA; MINB: resident CTAs per SM the register
+// allocation is sized for.  Variants (autotuned): 8 warps / 3 CTAs (80
+// registers, spill-free), 4 warps / 7 CTAs (72) and 4 warps / 8 CTAs (64).
+template <bool ENERGY, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(Dev d, int w0, int w1, int nblk_pairs, int a0, int a1) {
+    __shared__ PairShared<WARPS> sh;
     if (blockIdx.x >= nblk_pairs) {
-        alch_items<ENERGY>(d, w0, w1, a0, a1, blockIdx.x - nblk_pairs, gridDim.x - nblk_pairs);
+        alch_items<ENERGY, WARPS>(d, w0, w1, a0, a1, blockIdx.x - nblk_pairs, gridDim.x - nblk_pairs);
         return;
     }
     if (threadIdx.x == 0) {
@@ -346,23 +347,29 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, MINB) k_pairs(Dev d, int w0, 
         sh.pre[w1 - w0] = acc;
     }
     __syncthreads();
-    normal_items<ENERGY>(d, w0, w1, nblk_pairs, sh);
+    normal_items<ENERGY, WARPS>(d, w0, w1, nblk_pairs, sh);
 }
 
-void launch_pairs(const Dev &d, const HostView &hv, int w0, int w1, bool energy, cudaStream_t s) {
-    int nblk = hv.pair_blocks;
-    if (w1 - w0 < hv.n_walkers) {  // one walker: size the grid to its work
+template <bool ENERGY, int WARPS, int MINB>
+static void launch_pairs_v(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s) {
+    int nblk = hv.pair_blocks * 8 / WARPS;  // pair_blocks counts 8-warp CTAs
+    if (w1 - w0 < hv.n_walkers) {           // a subset of walkers: size the grid to its work
         int items = 0;
         for (int w = w0; w < w1; ++w) items += hv.item_cap[w];
-        int need = (items + PAIR_WARPS - 1) / PAIR_WARPS;
+        int need = (items + WARPS - 1) / WARPS;
         nblk = need < nblk ? need : nblk;
         nblk = nblk < 1 ? 1 : nblk;
     }
     const int a0 = hv.alch_base[w0], a1 = hv.alch_base[w1 - 1] + hv.n_alch[w1 - 1];
-    int ablk = (a1 - a0 + PAIR_WARPS - 1) / PAIR_WARPS;
-    if (energy) k_pairs<true, 3><<<nblk + ablk, PAIR_WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1);
-    else if (hv.pair_minb >= 4) k_pairs<false, 4><<<nblk + ablk, PAIR_WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1);
-    else k_pairs<false, 3><<<nblk + ablk, PAIR_WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1);
+    const int ablk = (a1 - a0 + WARPS - 1) / WARPS;
+    k_pairs<ENERGY, WARPS, MINB><<<nblk + ablk, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1);
+}
+
+void launch_pairs(const Dev &d, const HostView &hv, int w0, int w1, bool energy, cudaStream_t s) {
+    if (energy) launch_pairs_v<true, 8, 3>(d, hv, w0, w1, s);
+    else if (hv.pair_variant == 1) launch_pairs_v<false, 4, 7>(d, hv, w0, w1, s);
+    else if (hv.pair_variant == 2) launch_pairs_v<false, 4, 8>(d, hv, w0, w1, s);
+    else launch_pairs_v<false, 8, 3>(d, hv, w0, w1, s);
 }
 
 }  // namespace labf

@@ -834,7 +834,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         char key[256];
         snprintf(key, sizeof key, "dev%d-sm%d-W%d-slots%lld-ent%d", dev, h->n_sm, L.W, L.slots, L.ent_cap);
         auto it = tune_cache().find(key);
-        int best_c = 4, best_k = L.chunk, best_m = 3;
+        int best_c = 4, best_k = L.chunk, best_m = 0;
         if (it != tune_cache().end()) {
             best_c = it->second[0];
             best_k = it->second[1];
@@ -844,9 +844,9 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
             float best = 1e30f;
             const int ctas[] = {2, 3, 4, 6, 8};
             const int chunksz[] = {32, 64};  // item capacity was sized for L.chunk = 32
-            const int minbs[] = {3, 4};
-            for (int m : minbs) {
-                h->hv.pair_minb = m;
+            const int variants[] = {0, 1, 2};
+            for (int m : variants) {
+                h->hv.pair_variant = m;
                 for (int k : chunksz) {
                     if (k < L.chunk) continue;
                     d.chunk = k;
@@ -871,22 +871,20 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
             tune_cache()[key] = {best_c, best_k, best_m};
         }
         d.chunk = best_k;
-        h->hv.pair_minb = best_m;
+        h->hv.pair_variant = best_m;
         set_pair_blocks(h, best_c);
         rc = upload();
         if (rc != LA_OK) return rc;
         h->steps = 0;
         rc = prime(h, 0, L.W, true, false, s);
         if (rc != LA_OK) return rc;
-        snprintf(rep, sizeof rep,
-                 "autotuned: pair CTAs/SM=%d, entries/item=%d, registers sized for %d CTAs/SM, warps/CTA=8, "
-                 "graph steps=%d",
-                 best_c, best_k, best_m, h->graph_steps);
-    } else {
-        snprintf(rep, sizeof rep,
-                 "default: pair CTAs/SM=%d, entries/item=%d, registers sized for %d CTAs/SM, warps/CTA=8, "
-                 "graph steps=%d",
-                 h->hv.pair_blocks / h->n_sm, d.chunk, h->hv.pair_minb, h->graph_steps);
+    }
+    {
+        static const char *vname[] = {"8 warps/CTA, 80 registers", "4 warps/CTA, 72 registers",
+                                      "4 warps/CTA, 64 registers"};
+        snprintf(rep, sizeof rep, "%s: pair grid=%d x 8-warp CTAs per SM, %s, entries/item=%d, graph steps=%d",
+                 h->opt.autotune ? "autotuned" : "default", h->hv.pair_blocks / h->n_sm,
+                 vname[h->hv.pair_variant], d.chunk, h->graph_steps);
     }
     h->report = rep;
     rc = capture_graph(h);
