@@ -97,7 +97,8 @@ typedef struct la_handle la_handle;
  *   interval [stage_lo, stage_hi], stage_bins bins and stage_walkers
  *   walkers (walkers are ordered by stage).  The bias is
  *   min(1, n_k / n_full) * (bin mean); walkers merge their samples into the
- *   shared statistics every shared_freq steps.  abf_on = 0 disables the bias.
+ *   shared statistics every shared_freq steps (shared_freq = 0: only when the
+ *   host calls la_abf_import).  abf_on = 0 disables the bias.
  *
  *   Initial state: x0, v0 are [W][n_atoms][3] float32 (W = total walkers of
  *   the system), lam0 and plam0 are [W] double.  Philox streams are keyed by
@@ -127,6 +128,10 @@ typedef struct {
     const int32_t *stage_bins, *stage_walkers;
     const float *x0, *v0;       /* [W][n_atoms][3] */
     const double *lam0, *plam0; /* [W] */
+    /* lambda-dependent distance restraint (Sec. 4.2): each atom pair in
+     * lr_ij ([n_lr][2]) gets 1/2 lr_k (d - d_min)^2 while d < d_min(lambda) =
+     * lr_delta/2 (1 - cos 2 pi lambda), and contributes to dU/dlambda */
+    int32_t n_lr; const int32_t *lr_ij; double lr_delta, lr_k;
 } la_system_desc;
 
 /* Engine options; zero-initialise for defaults. */
@@ -193,6 +198,30 @@ int la_step_walkers_plain(la_handle *h, int64_t n_steps, void *stream);
 #define LA_WARN_EMPTY_BIN 1
 int la_read_abf(la_handle *h, int sys, int stage, double *sum, double *sumsq, int64_t *count,
                 double *grad, double *A, double *dA, double *dA_se, void *stream);
+
+/*
+ * la_abf_export / la_abf_import: host-level sharing of the accumulator
+ * between engines (walkers on other GPUs or processes; Sec. 2.4: walkers
+ * periodically share their mean-force estimates).  Use with shared_freq = 0,
+ * which disables the on-device merge: every walker then biases with the
+ * shared statistics plus its own samples since the last exchange.  Engines
+ * whose walkers cooperate must use distinct seeds (the Philox key is
+ * (seed, walker index within the handle's system)), or their noise coincides.
+ * la_abf_export fills host [n_bins] arrays with the stage's unmerged
+ * statistics summed over its walkers in walker order (sum, sumsq: double;
+ * count: int64).  la_abf_import adds host [n_bins] totals (normally the
+ * rank-ordered sum of every engine's export, so that all engines keep
+ * identical shared statistics) to the shared statistics, clears the stage's
+ * unmerged statistics and re-evaluates the lambda force of every walker with
+ * the new bias; it takes effect from the next step's first lambda half-kick.
+ * Call both between la_step_walkers calls.  Errors: LA_ERR_INVALID_ARG for a
+ * bad system/stage, a NULL pointer or a negative count (nothing is changed);
+ * device errors as for la_step_walkers.  Both synchronising.
+ */
+int la_abf_export(la_handle *h, int sys, int stage, double *sum, double *sumsq, int64_t *count,
+                  void *stream);
+int la_abf_import(la_handle *h, int sys, int stage, const double *sum, const double *sumsq,
+                  const int64_t *count, void *stream);
 
 /*
  * la_energy_forces: energies and forces of one walker (global walker index)

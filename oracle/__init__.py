@@ -74,6 +74,7 @@ class _System(C.Structure):
         ("fb_d0", C.c_double), ("fb_k", C.c_double),
         ("n_lh", C.c_int), ("lh_idx", C.c_void_p), ("lh_x0", C.c_void_p),
         ("lh_k0", C.c_double), ("lh_k1", C.c_double), ("lh_dims", C.c_int),
+        ("n_lr", C.c_int), ("lr_ij", C.c_void_p), ("lr_delta", C.c_double), ("lr_k", C.c_double),
         ("r_cut", C.c_double), ("eps_rf", C.c_double), ("coul", C.c_double),
         ("b_v", C.c_double), ("b_e", C.c_double),
         ("sc_alpha", C.c_double), ("sc_n", C.c_int), ("sc_m", C.c_int),
@@ -176,6 +177,9 @@ class OracleSystem:
         s.lh_idx = arr("lh_idx", spec.lh_idx, np.int32)
         s.lh_x0 = arr("lh_x0", spec.lh_x0.reshape(-1, 3), np.float64)
         s.lh_k0, s.lh_k1, s.lh_dims = float(spec.lh_k0), float(spec.lh_k1), int(spec.lh_dims)
+        s.n_lr = len(spec.lr_ij)
+        s.lr_ij = arr("lr_ij", np.asarray(spec.lr_ij).reshape(-1, 2), np.int32)
+        s.lr_delta, s.lr_k = float(spec.lr_delta), float(spec.lr_k)
         s.r_cut, s.eps_rf, s.coul = float(spec.r_cut), float(spec.eps_rf), float(spec.coul)
         s.b_v, s.b_e = float(spec.b_v), float(spec.b_e)
         s.sc_alpha, s.sc_n, s.sc_m = float(spec.sc_alpha), int(spec.sc_n), int(spec.sc_m)

@@ -458,6 +458,28 @@ static void energy_forces_impl(const or_system *sys, const double *x, double lam
     }
     dth[P - 1] = dk1;
 
+    /* ---- lambda-dependent distance restraint (Sec. 4.2): the pair is kept
+       at least d_min(lambda) = delta/2 (1 - cos 2 pi lambda) apart ---- */
+    if (sys->n_lr > 0) {
+        double dmin = 0.5 * sys->lr_delta * (1.0 - cos(2.0 * M_PI * lam));
+        double ddmin = sys->lr_delta * M_PI * sin(2.0 * M_PI * lam); /* d d_min / d lambda */
+        for (int p = 0; p < sys->n_lr; ++p) {
+            int a = sys->lr_ij[2 * p], b = sys->lr_ij[2 * p + 1];
+            double d[3];
+            for (int c = 0; c < 3; ++c) d[c] = min_image(x[3 * a + c] - x[3 * b + c], L);
+            double r = sqrt(dot3(d, d));
+            if (r >= dmin) continue;
+            double ex = r - dmin; /* negative */
+            terms[6] += 0.5 * sys->lr_k * ex * ex;
+            dUdl_direct += -sys->lr_k * ex * ddmin;
+            double fs = -sys->lr_k * ex / r; /* F_a = fs * d */
+            for (int c = 0; c < 3; ++c) {
+                F[3 * a + c] += fs * d[c];
+                F[3 * b + c] -= fs * d[c];
+            }
+        }
+    }
+
     dl[0] = dUdlv;
     dl[1] = dUdle;
     dl[2] = dUdl_direct;

@@ -41,6 +41,9 @@ typedef struct {
     /* lambda-switched harmonic well: U = 1/2 ((1-lam) k0 + lam k1) |x - x0|^2 over
        the first lh_dims Cartesian components */
     int n_lh; const int32_t *lh_idx; const double *lh_x0; double lh_k0, lh_k1; int lh_dims;
+    /* lambda-dependent distance restraint (Sec. 4.2): for each atom pair,
+       1/2 k (d - d_min)^2 when d < d_min(lambda) = delta/2 (1 - cos 2 pi lambda) */
+    int n_lr; const int32_t *lr_ij; double lr_delta, lr_k;
     double r_cut, eps_rf, coul; /* eps_rf <= 0 means a conducting (infinite) continuum */
     double b_v, b_e;            /* lambda -> (lambda_v, lambda_e) breakpoints */
     double sc_alpha; int sc_n, sc_m;

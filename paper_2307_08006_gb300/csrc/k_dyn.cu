@@ -287,6 +287,30 @@ __global__ void k_walker(Dev d, int w0) {
 
     // ---- lambda-switched harmonic well (uses lambda itself) ----
     double dl_dir = 0.0, e_lh = 0.0, dk1 = 0.0, d2k1 = 0.0;
+    // ---- lambda-dependent distance restraint (Sec. 4.2): pairs kept at
+    // least d_min = delta/2 (1 - cos 2 pi lambda) apart ----
+    if (S.n_lr > 0) {
+        const double lam = d.lam[w];
+        const double dmin = 0.5 * S.lr_delta * (1.0 - cospi(2.0 * lam));
+        const double ddmin = S.lr_delta * 3.14159265358979323846 * sinpi(2.0 * lam);
+        for (int k = tid; k < S.n_lr; k += nt) {
+            const int2 ab = d.lr_ij[S.lr_off + k];
+            const int ga = soa[ab.x], gb = soa[ab.y];
+            const float4 xa = d.xq[ga], xb = d.xq[gb];
+            const float dx = min_image(xa.x - xb.x, S.boxf, S.box_invf);
+            const float dy = min_image(xa.y - xb.y, S.boxf, S.box_invf);
+            const float dz = min_image(xa.z - xb.z, S.boxf, S.box_invf);
+            const double r = sqrt((double)dx * dx + (double)dy * dy + (double)dz * dz);
+            if (r < dmin) {
+                const double ex = r - dmin;
+                e_lh += 0.5 * S.lr_k * ex * ex;
+                dl_dir += -S.lr_k * ex * ddmin;
+                const float fs = (float)(-S.lr_k * ex / r);
+                add_force(d, ga, fs * dx, fs * dy, fs * dz);
+                add_force(d, gb, -fs * dx, -fs * dy, -fs * dz);
+            }
+        }
+    }
     if (S.n_lh > 0) {
         const double lam = d.lam[w];
         const double kl = (1.0 - lam) * S.lh_k0 + lam * S.lh_k1;
@@ -399,8 +423,8 @@ __global__ void k_lambda(Dev d, int s0, int prime) {
         }
         __syncthreads();
         const unsigned long long stepn = d.step[st.w0] + 1ull;
-        const int K = S.shared_freq > 0 ? S.shared_freq : 1;
-        if (stepn % (unsigned long long)K == 0ull) {
+        const int K = S.shared_freq;  // 0: merged only by the host (la_abf_import)
+        if (K > 0 && stepn % (unsigned long long)K == 0ull) {
             for (int k = tid; k < st.n_bins; k += nt) {
                 double s1 = d.abf_sum[st.bin_off + k], s2 = d.abf_sumsq[st.bin_off + k];
                 unsigned long long c = d.abf_count[st.bin_off + k];

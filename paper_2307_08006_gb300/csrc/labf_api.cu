@@ -32,7 +32,7 @@ struct Layout {
     std::vector<SysLayout> sys;
     int W = 0, n_stages = 0, total_bins = 0, max_bins = 0, P_max = 1;
     long long slots = 0, scs = 0, cols = 0, atoms_w = 0, alch_w = 0, items = 0, bo = 0;
-    long long atoms_s = 0, alch_s = 0, bonds = 0, angles = 0, posres = 0, fb = 0, lh = 0;
+    long long atoms_s = 0, alch_s = 0, bonds = 0, angles = 0, posres = 0, fb = 0, lh = 0, lr = 0;
     int ent_cap = 0, alch_cap = 0, chunk = 32, max_n = 0, ncs = 1, sub_cap = 0;
     size_t bytes = 0;
 };
@@ -72,7 +72,7 @@ int validate(const la_system_desc *sys, int n_sys, std::string &err) {
         if (!(S.box > 0) || !(S.r_cut > 0) || !(S.skin >= 0) || !(S.dt > 0) || !(S.kT > 0) ||
             !(S.m_lambda > 0) || S.n_stages <= 0 || S.n_stages > 16 || !S.stage_lo || !S.stage_hi ||
             !S.stage_bins || !S.stage_walkers || !(S.b_v > 0) || !(S.b_e < 1) || S.sc_n < 0 ||
-            S.sc_m < 0 || !(S.n_full > 0)) {
+            S.sc_m < 0 || !(S.n_full > 0) || S.shared_freq < 0) {
             snprintf(buf, sizeof buf, "system %d: invalid parameters", s);
             err = buf;
             return LA_ERR_INVALID_ARG;
@@ -107,7 +107,7 @@ int validate(const la_system_desc *sys, int n_sys, std::string &err) {
         };
         if (!chk(S.n_bonds, S.bond_ij, 2) || !chk(S.n_angles, S.angle_ijk, 3) ||
             !chk(S.n_posres, S.posres_idx, 1) || !chk(S.n_fb_a, S.fb_a, 1) || !chk(S.n_fb_b, S.fb_b, 1) ||
-            !chk(S.n_lh, S.lh_idx, 1)) {
+            !chk(S.n_lh, S.lh_idx, 1) || !chk(S.n_lr, S.lr_ij, 2)) {
             snprintf(buf, sizeof buf, "system %d: topology index out of range", s);
             err = buf;
             return LA_ERR_INVALID_ARG;
@@ -185,6 +185,7 @@ void compute_layout(const la_system_desc *sys, int n_sys, const la_options *opt,
         L.posres += S.n_posres;
         L.fb += S.n_fb_a + S.n_fb_b;
         L.lh += S.n_lh;
+        L.lr += S.n_lr;
     }
     // the cyclic half list gives each super-cluster about half its neighbourhood
     L.ent_cap = (int)std::ceil(fac * 0.6 * ent_est) + 64;
@@ -217,6 +218,7 @@ size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io
     d.fb_idx = a.take<int>(std::max<long long>(1, L.fb));
     d.lh_idx = a.take<int>(std::max<long long>(1, L.lh));
     d.lh_x0 = a.take<float4>(std::max<long long>(1, L.lh));
+    d.lr_ij = a.take<int2>(std::max<long long>(1, L.lr));
     d.xq = a.take<float4>(L.slots);
     d.vv = a.take<float4>(L.slots);
     d.xref = a.take<float4>(L.slots);
@@ -573,6 +575,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
     std::vector<float2> bp, angp;
     std::vector<int4> aijk;
     std::vector<int> pidx, fbidx, lhidx;
+    std::vector<int2> lrij;
     std::vector<float4> px0, lhx0;
     int atom_off = 0, alch_off = 0, stage_idx = 0, bin_off = 0;
     int w_glob = 0;
@@ -655,6 +658,11 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         D.lh_dims = S.lh_dims;
         D.lh_k0 = S.lh_k0;
         D.lh_k1 = S.lh_k1;
+        D.lr_off = (int)lrij.size();
+        D.n_lr = S.n_lr;
+        D.lr_delta = S.lr_delta;
+        D.lr_k = S.lr_k;
+        for (int b = 0; b < S.n_lr; ++b) lrij.push_back(make_int2(S.lr_ij[2 * b], S.lr_ij[2 * b + 1]));
         for (int b = 0; b < S.n_lh; ++b) {
             lhidx.push_back(S.lh_idx[b]);
             lhx0.push_back(make_float4((float)S.lh_x0[3 * b], (float)S.lh_x0[3 * b + 1],
@@ -664,7 +672,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         D.lambda_dynamics = S.lambda_dynamics;
         D.abf_on = S.abf_on;
         D.theta_stats = S.theta_stats;
-        D.shared_freq = S.shared_freq > 0 ? S.shared_freq : 1;
+        D.shared_freq = S.shared_freq > 0 ? S.shared_freq : 0;  // 0: host-managed merging
         D.n_full = S.n_full;
         D.w_first = w_glob;
         D.w_count = sl.W;
@@ -785,6 +793,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
     CU(h, up((void *)d.fb_idx, fbidx.data(), sizeof(int) * fbidx.size()));
     CU(h, up((void *)d.lh_idx, lhidx.data(), sizeof(int) * lhidx.size()));
     CU(h, up((void *)d.lh_x0, lhx0.data(), sizeof(float4) * lhx0.size()));
+    CU(h, up((void *)d.lr_ij, lrij.data(), sizeof(int2) * lrij.size()));
     CU(h, up(d.xq, xq0.data(), sizeof(float4) * xq0.size()));
     CU(h, up(d.vv, vv0.data(), sizeof(float4) * vv0.size()));
     CU(h, up(d.xref, xq0.data(), sizeof(float4) * xq0.size()));
@@ -1083,6 +1092,70 @@ int la_set_alch_params(la_handle *h, int sys, const double *theta, void *stream)
     while (w1 < h->L.W && h->walk[w1].sys == sys) ++w1;
     int rc = prime(h, w0, w1, true, false, s);
     if (rc != LA_OK) return rc;
+    return sync_status(h, s, nullptr);
+}
+
+int la_abf_export(la_handle *h, int sys, int stage, double *sum, double *sumsq, int64_t *count, void *stream) {
+    if (!h || !sum || !sumsq || !count) return LA_ERR_INVALID_ARG;
+    if (sys < 0 || sys >= (int)h->sys.size() || stage < 0 || stage >= h->sys_nstage[sys])
+        return fail(h, LA_ERR_INVALID_ARG, "bad system/stage");
+    cudaStream_t s = (cudaStream_t)stream;
+    const StageDev &st = h->stages[h->sys_stage0[sys] + stage];
+    const int MB = h->L.max_bins, nw = st.w1 - st.w0;
+    std::vector<double> a((size_t)nw * MB), b((size_t)nw * MB);
+    std::vector<unsigned long long> c((size_t)nw * MB);
+    CU(h, cudaMemcpyAsync(a.data(), h->d.dl_sum + (size_t)st.w0 * MB, sizeof(double) * a.size(), cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(b.data(), h->d.dl_sumsq + (size_t)st.w0 * MB, sizeof(double) * b.size(), cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(c.data(), h->d.dl_count + (size_t)st.w0 * MB, sizeof(unsigned long long) * c.size(),
+                          cudaMemcpyDeviceToHost, s));
+    int rc = sync_status(h, s, nullptr);
+    if (rc != LA_OK) return rc;
+    for (int k = 0; k < st.n_bins; ++k) {
+        double s1 = 0.0, s2 = 0.0;
+        unsigned long long n = 0;
+        for (int w = 0; w < nw; ++w) {  // walker order
+            s1 += a[(size_t)w * MB + k];
+            s2 += b[(size_t)w * MB + k];
+            n += c[(size_t)w * MB + k];
+        }
+        sum[k] = s1;
+        sumsq[k] = s2;
+        count[k] = (int64_t)n;
+    }
+    return LA_OK;
+}
+
+int la_abf_import(la_handle *h, int sys, int stage, const double *sum, const double *sumsq, const int64_t *count,
+                  void *stream) {
+    if (!h || !sum || !sumsq || !count) return LA_ERR_INVALID_ARG;
+    if (sys < 0 || sys >= (int)h->sys.size() || stage < 0 || stage >= h->sys_nstage[sys])
+        return fail(h, LA_ERR_INVALID_ARG, "bad system/stage");
+    cudaStream_t s = (cudaStream_t)stream;
+    const StageDev &st = h->stages[h->sys_stage0[sys] + stage];
+    const int nb = st.n_bins, MB = h->L.max_bins;
+    std::vector<double> s1(nb), s2(nb);
+    std::vector<unsigned long long> c(nb);
+    CU(h, cudaMemcpyAsync(s1.data(), h->d.abf_sum + st.bin_off, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(s2.data(), h->d.abf_sumsq + st.bin_off, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    CU(h, cudaMemcpyAsync(c.data(), h->d.abf_count + st.bin_off, sizeof(unsigned long long) * nb,
+                          cudaMemcpyDeviceToHost, s));
+    CU(h, cudaStreamSynchronize(s));
+    for (int k = 0; k < nb; ++k) {
+        if (count[k] < 0) return fail(h, LA_ERR_INVALID_ARG, "negative count");
+        s1[k] += sum[k];
+        s2[k] += sumsq[k];
+        c[k] += (unsigned long long)count[k];
+    }
+    CU(h, cudaMemcpyAsync(h->d.abf_sum + st.bin_off, s1.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+    CU(h, cudaMemcpyAsync(h->d.abf_sumsq + st.bin_off, s2.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+    CU(h, cudaMemcpyAsync(h->d.abf_count + st.bin_off, c.data(), sizeof(unsigned long long) * nb,
+                          cudaMemcpyHostToDevice, s));
+    const size_t rows = (size_t)(st.w1 - st.w0) * MB;
+    CU(h, cudaMemsetAsync(h->d.dl_sum + (size_t)st.w0 * MB, 0, sizeof(double) * rows, s));
+    CU(h, cudaMemsetAsync(h->d.dl_sumsq + (size_t)st.w0 * MB, 0, sizeof(double) * rows, s));
+    CU(h, cudaMemsetAsync(h->d.dl_count + (size_t)st.w0 * MB, 0, sizeof(unsigned long long) * rows, s));
+    // refresh the lambda forces with the new bias
+    launch_lambda(h->d, 0, (int)h->stages.size(), true, s);
     return sync_status(h, s, nullptr);
 }
 

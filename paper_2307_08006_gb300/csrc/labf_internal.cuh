@@ -61,6 +61,8 @@ struct SysDev {
     float fb_d0, fb_k;
     int lh_off, n_lh, lh_dims;
     double lh_k0, lh_k1;
+    int lr_off, n_lr;             // lambda-dependent distance restraints
+    double lr_delta, lr_k;
     uint32_t seed;
     int lambda_dynamics, abf_on, theta_stats, shared_freq;
     double n_full;
@@ -110,6 +112,7 @@ struct Dev {
     const int *fb_idx;            // group a then group b
     const int *lh_idx;
     const float4 *lh_x0;
+    const int2 *lr_ij;
     // per slot
     float4 *xq, *vv, *xref;
     float2 *lj, *im;

@@ -30,7 +30,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "BOX_TOO_SMALL", -3: "CUDA", -4: "UNSUPPORTED",
           -6: "LIST_OVERFLOW", -7: "NONFINITE", -8: "FIXED_OVERFLOW", -9: "STATE"}
 
 EXPORTED = ("la_query_sizes", "la_create_system", "la_step_walkers", "la_step_walkers_plain",
-            "la_read_abf", "la_energy_forces", "la_get_state", "la_set_state", "la_set_alch_params",
+            "la_read_abf", "la_abf_export", "la_abf_import", "la_energy_forces", "la_get_state", "la_set_state", "la_set_alch_params",
             "la_read_theta", "la_get_pairs", "la_lambda_path", "la_sync", "la_stats",
             "la_time_kernels", "la_autotune_report", "la_last_error", "la_destroy",
             "la_alch_pairs_static", "la_static_last_error")
@@ -67,6 +67,7 @@ class la_system_desc(C.Structure):
         ("stage_lo", C.c_void_p), ("stage_hi", C.c_void_p), ("stage_bins", C.c_void_p),
         ("stage_walkers", C.c_void_p),
         ("x0", C.c_void_p), ("v0", C.c_void_p), ("lam0", C.c_void_p), ("plam0", C.c_void_p),
+        ("n_lr", C.c_int32), ("lr_ij", C.c_void_p), ("lr_delta", C.c_double), ("lr_k", C.c_double),
     ]
 
 
@@ -101,6 +102,8 @@ def load(build_if_missing: bool = False):
     lib.la_step_walkers.argtypes = [H, C.c_int64, P]
     lib.la_step_walkers_plain.argtypes = [H, C.c_int64, P]
     lib.la_read_abf.argtypes = [H, I, I, P, P, P, P, P, P, P, P]
+    lib.la_abf_export.argtypes = [H, I, I, P, P, P, P]
+    lib.la_abf_import.argtypes = [H, I, I, P, P, P, P]
     lib.la_energy_forces.argtypes = [H, I, C.c_uint32, P, P, P, P, P, P]
     lib.la_get_state.argtypes = [H, I, P, P, P, P, P, P]
     lib.la_set_state.argtypes = [H, I, P, P, P, P, P]
@@ -193,6 +196,9 @@ def make_desc(spec, run, state, keep: _Keep) -> la_system_desc:
     d.v0 = k.arr(state.v, np.float32)
     d.lam0 = k.arr(state.lam, np.float64)
     d.plam0 = k.arr(state.plam, np.float64)
+    d.n_lr = len(spec.lr_ij)
+    d.lr_ij = k.arr(np.asarray(spec.lr_ij).reshape(-1, 2), np.int32)
+    d.lr_delta, d.lr_k = float(spec.lr_delta), float(spec.lr_k)
     return d
 
 
@@ -291,6 +297,25 @@ class Engine:
         self._check(rc)
         return dict(sum=s1, sumsq=s2, count=cnt, grad=grad, A=A, dA=dA.value, dA_se=se.value,
                     empty_bin=rc == LA_WARN_EMPTY_BIN)
+
+    def abf_export(self, sys: int = 0, stage: int = 0, stream=None):
+        """Unmerged bin statistics of the stage's walkers, summed in walker order."""
+        nb = self.systems[sys].run.stages[stage].n_bins
+        s1, s2, cnt = np.zeros(nb), np.zeros(nb), np.zeros(nb, np.int64)
+        self._check(self.lib.la_abf_export(self.handle, sys, stage, _p(s1), _p(s2), _p(cnt),
+                                           self._stream(stream)))
+        return s1, s2, cnt
+
+    def abf_import(self, sum, sumsq, count, sys: int = 0, stage: int = 0, stream=None) -> None:
+        """Add host totals to the shared statistics; clears the unmerged ones."""
+        nb = self.systems[sys].run.stages[stage].n_bins
+        s1 = np.ascontiguousarray(sum, np.float64)
+        s2 = np.ascontiguousarray(sumsq, np.float64)
+        cnt = np.ascontiguousarray(count, np.int64)
+        if s1.shape != (nb,) or s2.shape != (nb,) or cnt.shape != (nb,):
+            raise ValueError(f"abf_import wants [{nb}] arrays")
+        self._check(self.lib.la_abf_import(self.handle, sys, stage, _p(s1), _p(s2), _p(cnt),
+                                           self._stream(stream)))
 
     def energy_forces(self, walker: int, rebuild: bool = False, count_pairs: bool = False,
                       forces: bool = True, stream=None) -> dict:

@@ -69,6 +69,11 @@ class SystemSpec:
     lh_k0: float = 0.0
     lh_k1: float = 0.0
     lh_dims: int = 3
+    # lambda-dependent distance restraint: atom pairs kept at least
+    # delta/2 (1 - cos 2 pi lambda) apart with force constant lr_k
+    lr_ij: np.ndarray = field(default_factory=lambda: np.zeros((0, 2), np.int32))
+    lr_delta: float = 0.0
+    lr_k: float = 0.0
     r_cut: float = 1.0
     eps_rf: float = 78.0
     coul: float = COULOMB_KJ_NM
@@ -439,7 +444,8 @@ def initial_state(spec: SystemSpec, run: RunSpec, seed: int | None = None,
     rng = np.random.default_rng(run.seed if seed is None else seed)
     W, n = run.n_walkers, spec.n
     x = np.broadcast_to(spec.x, (W, n, 3)).astype(np.float32).copy()
-    sd = np.sqrt(run.kT / spec.mass)[None, :, None]
+    with np.errstate(divide="ignore"):  # a massless atom is refused by the engine
+        sd = np.sqrt(run.kT / spec.mass)[None, :, None]
     v = (rng.standard_normal((W, n, 3)) * sd).astype(np.float32)
     stages = run.walker_stage()
     if lam0 is None:

@@ -105,6 +105,30 @@ def test_forces_lj_fluid():
         check_forces(eng, sp, st, w)
 
 
+@pytest.mark.parametrize("lam0", [[0.03, 0.25, 0.45, 0.5], [0.5, 0.55, 0.74, 0.98]])
+def test_restraint_terms(lam0):
+    """Positional, flat-bottom COM, lambda-switched well and lambda-dependent
+    distance restraints (Sec. 3.1 restraint set) against the oracle."""
+    sp = small_water(jitter=0.01)
+    n = sp.n
+    x = sp.x.astype(np.float64)
+    sp = synth.with_changes(
+        sp, posres_idx=np.array([0, 3], np.int32), posres_x0=x[[0, 3]] + 0.05, posres_k=1000.0,
+        fb_a=np.arange(n - 4, n, dtype=np.int32), fb_b=np.array([6, 9, 12], np.int32),
+        fb_d0=0.05, fb_k=800.0, lh_idx=np.array([n - 1], np.int32), lh_x0=x[[n - 1]] + 0.07,
+        lh_k0=100.0, lh_k1=400.0, lh_dims=3, lr_ij=np.array([[n - 3, 9], [2, 20], [n - 1, 40]], np.int32),
+        lr_delta=1.2, lr_k=500.0)
+    run = synth.water_run(walkers_per_stage=2, n_bins=20)
+    eng, st = make_engine(sp, run, lam0=lam0)
+    no_lr = oracle.OracleSystem(synth.with_changes(sp, lr_ij=np.zeros((0, 2), np.int32)))
+    active = 0
+    for w in range(run.n_walkers):
+        g, ref = check_forces(eng, sp, st, w)
+        r0 = oracle.energy_forces(no_lr, st.x[w].astype(np.float64), st.lam[w])
+        active += ref["terms"][6] != r0["terms"][6]
+    assert active > 0  # the distance restraints act at some of these lambdas
+
+
 def test_theta_derivatives():
     sp = small_water(jitter=0.01)
     run = synth.water_run(walkers_per_stage=2, n_bins=20)

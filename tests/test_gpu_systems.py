@@ -203,6 +203,70 @@ def test_shared_freq_merge_matches_oracle():
 
 
 # ---------------------------------------------------------------------------
+# host-level sharing across engines (Sec. 2.4 walkers on several GPUs)
+# ---------------------------------------------------------------------------
+def _sharing_inputs(seed, shared_freq):
+    sp = jittered(synth.water_box(100, 6, seed=91, box=1.5, r_cut=0.6), 91)
+    run = synth.water_run(seed=seed, walkers_per_stage=2, n_bins=10)
+    run.shared_freq = shared_freq
+    st = synth.initial_state(sp, run, lam0=[0.1, 0.3, 0.6, 0.8])
+    return sp, run, st
+
+
+def test_export_import_equals_device_merge():
+    K = 6
+    sp, run_h, st = _sharing_inputs(92, 0)
+    _, run_d, _ = _sharing_inputs(92, K)
+    host = labf.engine_for(sp, run_h, st, options=dict(autotune=0))
+    dev = labf.engine_for(sp, run_d, st, options=dict(autotune=0))
+    # identical until the device merge at step K (the samples of step K are
+    # folded before it), so the host's export must equal the merged result
+    host.step(K)
+    dev.step(K)
+    for stage in range(2):
+        assert host.read_abf(0, stage)["count"].sum() == 0
+        s1, s2, c = host.abf_export(0, stage)
+        d = dev.read_abf(0, stage)
+        assert c.sum() == K * 2
+        assert np.array_equal(c, d["count"])
+        assert np.array_equal(s1, d["sum"]) and np.array_equal(s2, d["sumsq"])
+        host.abf_import(s1, s2, c, 0, stage)
+        h = host.read_abf(0, stage)
+        for key in ("sum", "sumsq", "count", "grad"):
+            assert np.array_equal(np.nan_to_num(h[key]), np.nan_to_num(d[key]))
+        z = host.abf_export(0, stage)
+        assert not any(np.any(a) for a in z)
+    with pytest.raises(labf.LabfError):
+        host.abf_import(s1, s2, -np.ones_like(c), 0, 0)
+    with pytest.raises(labf.LabfError):
+        host.abf_export(0, 5)
+
+
+def test_two_engines_share_statistics_in_rank_order():
+    from paper_2307_08006_gb300 import multiwalker
+    engines = []
+    for seed in (93, 94):
+        sp, run, st = _sharing_inputs(seed, 0)
+        engines.append(labf.engine_for(sp, run, st))
+    rounds, every = 3, 5
+    for _ in range(rounds):
+        for e in engines:
+            e.step(every)
+        for stage in range(2):
+            parts = [e.abf_export(0, stage) for e in engines]
+            tot = [multiwalker.reduce_in_rank_order([p[j] for p in parts]) for j in range(3)]
+            for e in engines:
+                e.abf_import(*tot, sys=0, stage=stage)
+    for stage in range(2):
+        a, b = engines[0].read_abf(0, stage), engines[1].read_abf(0, stage)
+        for key in ("sum", "sumsq", "count"):
+            assert np.array_equal(a[key], b[key])
+        assert int(a["count"].sum()) == rounds * every * 2 * len(engines)
+    # distinct seeds: the walkers do not move alike
+    assert not np.array_equal(engines[0].get_state(0)["x"], engines[1].get_state(0)["x"])
+
+
+# ---------------------------------------------------------------------------
 # error paths (no GPU fault: every write is bounds-checked, the status word
 # reports the condition)
 # ---------------------------------------------------------------------------

@@ -178,7 +178,8 @@ def _restrained_small(seed=4):
         sp, posres_idx=np.array([0, 3], np.int32), posres_x0=x[[0, 3]] + 0.05, posres_k=1000.0,
         fb_a=np.arange(n - 4, n, dtype=np.int32), fb_b=np.array([6, 9, 12], np.int32),
         fb_d0=0.05, fb_k=800.0, lh_idx=np.array([n - 1], np.int32), lh_x0=x[[n - 1]] + 0.07,
-        lh_k0=100.0, lh_k1=400.0, lh_dims=3)
+        lh_k0=100.0, lh_k1=400.0, lh_dims=3, lr_ij=np.array([[n - 3, 9], [2, 20]], np.int32),
+        lr_delta=1.2, lr_k=500.0)
     return sp, x
 
 
@@ -525,3 +526,21 @@ def test_masked_evaluation_matches_full():
         np.testing.assert_allclose(part["F"][atoms], full["F"][atoms], rtol=1e-12, atol=1e-10)
         assert part["dUdl"] == pytest.approx(full["dUdl"], rel=1e-12, abs=1e-12)
         np.testing.assert_allclose(part["dth"], full["dth"], rtol=1e-12, atol=1e-12)
+
+
+def test_lambda_dependent_restraint_endpoints():
+    """d_min(lambda) = delta/2 (1 - cos 2 pi lambda): no restraint at lambda = 0
+    and 1, full distance delta at lambda = 1/2 (Sec. 4.2)."""
+    r, delta, k = 0.3, 1.0, 500.0
+    sp = _two_atoms(r, sig=(0, 0), eps=(0, 0), rc=2.5)
+    sp = synth.with_changes(sp, lr_ij=np.array([[0, 1]], np.int32), lr_delta=delta, lr_k=k)
+    o = oracle.OracleSystem(sp)
+    x = sp.x.astype(np.float64)
+    ra = float(x[1, 0] - x[0, 0])
+    assert oracle.energy_forces(o, x, 0.0)["terms"][6] == 0.0
+    assert oracle.energy_forces(o, x, 1.0)["terms"][6] == pytest.approx(0.0, abs=1e-20)
+    mid = oracle.energy_forces(o, x, 0.5)
+    assert mid["terms"][6] == pytest.approx(0.5 * k * (ra - delta) ** 2, rel=1e-12)
+    assert mid["dUdl"] == pytest.approx(0.0, abs=1e-9)  # d_min is stationary at 1/2
+    q = oracle.energy_forces(o, x, 0.25)  # d_min = delta/2, slope delta pi
+    assert q["dl"][2] == pytest.approx(-k * (ra - 0.5 * delta) * delta * np.pi, rel=1e-12)
