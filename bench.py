@@ -163,8 +163,15 @@ def gpu_arm(args):
     dev = torch.device("cuda", local)
     spec, run = workload()
     state = synth.initial_state(spec, run, seed=run.seed + 1000 * rank)
-    eng = labf.Engine([labf.SystemInput(spec, run, state)],
-                      options=dict(graph_steps=args.graph_steps, autotune=int(args.autotune)), device=local)
+    opts = dict(graph_steps=args.graph_steps, autotune=int(args.autotune))
+    if args.launch:  # a fixed pair-kernel launch shape instead of the tuner's
+        for kv in args.launch.split(","):
+            k, v = kv.split("=")
+            if k not in ("pair_variant", "pair_ctas_per_sm", "chunk_entries"):
+                raise SystemExit(f"unknown launch option {k}")
+            opts[k] = int(v)
+        opts["autotune"] = 0
+    eng = labf.Engine([labf.SystemInput(spec, run, state)], options=opts, device=local)
     stream = torch.cuda.current_stream(dev)
     md = args.md_steps
     # settle the lattice start (untimed): 2 ps
@@ -335,6 +342,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch", default="",
+                    help="fixed pair-kernel shape, e.g. pair_variant=1,pair_ctas_per_sm=6,chunk_entries=64")
     ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
     args = ap.parse_args()
     os.makedirs(args.out_dir, exist_ok=True)

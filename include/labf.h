@@ -139,9 +139,10 @@ typedef struct {
     int32_t graph_steps;         /* MD steps captured per CUDA-graph replay (default 10) */
     int32_t autotune;            /* 1: pick pair-kernel launch shape by timing at create */
     double list_capacity_factor; /* >= 1 safety factor on list capacities (default 1.6) */
-    int32_t pair_warps;          /* warps per CTA of the pair kernel (0 = default) */
-    int32_t pair_ctas_per_sm;    /* resident CTAs per SM of the pair kernel (0 = default) */
-    int32_t chunk_entries;       /* cluster-pair entries per warp work item (0 = default) */
+    int32_t pair_variant;        /* pair kernel when not autotuned: 0 = 8 warps/CTA with 80
+                                    registers (default), 1 = 4 warps/72, 2 = 4 warps/64 */
+    int32_t pair_ctas_per_sm;    /* pair grid in 8-warp CTA equivalents per SM (0 = 4) */
+    int32_t chunk_entries;       /* cluster-pair entries per warp work item (0 = 32) */
 } la_options;
 
 /*

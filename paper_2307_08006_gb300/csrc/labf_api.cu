@@ -536,6 +536,11 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         return rc;
     }
     if (opt) h->opt = *opt;
+    if (h->opt.pair_variant < 0 || h->opt.pair_variant > 2) {
+        h->err = "pair_variant must be 0, 1 or 2";
+        *out = h;
+        return LA_ERR_INVALID_ARG;
+    }
     compute_layout(sys, n_sys, opt, h->L);
     const Layout &L = h->L;
     cudaStream_t s = (cudaStream_t)stream;
@@ -824,6 +829,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
     hv.bo_off = h->bo_off.data();
     hv.n_bo = h->n_bo.data();
     set_pair_blocks(h, h->opt.pair_ctas_per_sm > 0 ? h->opt.pair_ctas_per_sm : 4);
+    h->hv.pair_variant = h->opt.pair_variant;
     h->graph_steps = h->opt.graph_steps > 0 ? h->opt.graph_steps : 10;
 
     CU(h, cudaMallocHost((void **)&h->h_status, sizeof(unsigned)));
@@ -891,8 +897,8 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
     {
         static const char *vname[] = {"8 warps/CTA, 80 registers", "4 warps/CTA, 72 registers",
                                       "4 warps/CTA, 64 registers"};
-        snprintf(rep, sizeof rep, "%s: pair grid=%d x 8-warp CTAs per SM, %s, entries/item=%d, graph steps=%d",
-                 h->opt.autotune ? "autotuned" : "default", h->hv.pair_blocks / h->n_sm,
+        snprintf(rep, sizeof rep, "%s: pair grid=%d x 8-warp CTA equivalents per SM, %s, entries/item=%d, graph steps=%d",
+                 h->opt.autotune ? "autotuned" : "fixed", h->hv.pair_blocks / h->n_sm,
                  vname[h->hv.pair_variant], d.chunk, h->graph_steps);
     }
     h->report = rep;

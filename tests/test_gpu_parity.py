@@ -196,6 +196,26 @@ def test_repeat_runs_bit_identical():
     assert np.array_equal(outs[0][4], outs[1][4])
 
 
+def test_pair_kernel_launch_shapes_bit_identical():
+    """Every pair-kernel variant, grid size and work-item size gives the same
+    bits (per-tile arithmetic is shared; 64-bit fixed-point sums are
+    order-free)."""
+    sp = small_water(n_w=137, n_s=5, box=1.7, seed=5, jitter=0.03)
+    run = synth.water_run(walkers_per_stage=2, n_bins=20)
+    st = synth.initial_state(sp, run, lam0=[0.1, 0.3, 0.6, 0.8])
+    outs = []
+    for var, ctas, chunk in ((0, 4, 32), (1, 7, 32), (2, 8, 64), (1, 2, 64), (0, 1, 32)):
+        e, _ = make_engine(sp, run, state=st, pair_variant=var, pair_ctas_per_sm=ctas, chunk_entries=chunk)
+        e.step(30)
+        outs.append([e.get_state(w) for w in range(4)])
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v"], b["v"])
+            assert a["lam"] == b["lam"] and a["plam"] == b["plam"]
+    with pytest.raises(labf.LabfError):
+        make_engine(sp, run, state=st, pair_variant=3)
+
+
 def test_single_atom_system_and_rebuilds():
     sp = synth.harmonic_well(dims=3)
     run = synth.harmonic_run(n_walkers=4)
