@@ -22,6 +22,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import subprocess
 import sys
 import time
@@ -299,7 +300,10 @@ def gpu_arm(args):
             config=dict(workload=WORKLOAD, walkers=run.n_walkers, atoms_per_walker=spec.n,
                         md_steps_per_bench_step=md, l2="flushed between bench steps (256 MB write)",
                         parallelism="replicas" if world > 1 else "1 GPU, walkers batched",
-                        launch=eng.autotune_report()),
+                        launch=eng.autotune_report(),
+                        launch_options=",".join(
+                            f"{k}={v}" for k, v in re.findall(r"(pair_variant|pair_ctas_per_sm|chunk_entries)=(\d+)",
+                                                              eng.autotune_report()))),
             pair_interactions_per_s=pair_rate,
             in_cutoff_pairs_per_md_step=pairs_per_md,
             lists=dict(rebuilds_per_walker_md_step=rebuild_rate, cluster_pair_entries=list_entries,

@@ -536,8 +536,9 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         return rc;
     }
     if (opt) h->opt = *opt;
-    if (h->opt.pair_variant < 0 || h->opt.pair_variant > 2) {
-        h->err = "pair_variant must be 0, 1 or 2";
+    if (h->opt.pair_variant < 0 || h->opt.pair_variant >= LA_PAIR_VARIANTS ||
+        (h->opt.chunk_entries > 0 && h->opt.chunk_entries % 32 != 0)) {
+        h->err = "pair_variant must be in [0, 6) and chunk_entries a multiple of 32";
         *out = h;
         return LA_ERR_INVALID_ARG;
     }
@@ -859,7 +860,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
             float best = 1e30f;
             const int ctas[] = {2, 3, 4, 6, 8};
             const int chunksz[] = {32, 64};  // item capacity was sized for L.chunk = 32
-            const int variants[] = {0, 1, 2};
+            const int variants[] = {0, 1, 2, 3, 4, 5};
             for (int m : variants) {
                 h->hv.pair_variant = m;
                 for (int k : chunksz) {
@@ -895,11 +896,15 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         if (rc != LA_OK) return rc;
     }
     {
-        static const char *vname[] = {"8 warps/CTA, 80 registers", "4 warps/CTA, 72 registers",
-                                      "4 warps/CTA, 64 registers"};
-        snprintf(rep, sizeof rep, "%s: pair grid=%d x 8-warp CTA equivalents per SM, %s, entries/item=%d, graph steps=%d",
-                 h->opt.autotune ? "autotuned" : "fixed", h->hv.pair_blocks / h->n_sm,
-                 vname[h->hv.pair_variant], d.chunk, h->graph_steps);
+        static const char *vname[LA_PAIR_VARIANTS] = {
+            "scalar, 8 warps/CTA, 80 registers", "scalar, 4 warps/CTA, 72 registers",
+            "scalar, 4 warps/CTA, 64 registers", "packed FP32x2, 4 warps/CTA, 80 registers",
+            "packed FP32x2, 4 warps/CTA, 96 registers", "packed FP32x2, 8 warps/CTA, 80 registers"};
+        snprintf(rep, sizeof rep,
+                 "%s: pair_variant=%d (%s), pair_ctas_per_sm=%d (8-warp CTA equivalents), "
+                 "chunk_entries=%d, graph steps=%d",
+                 h->opt.autotune ? "autotuned" : "fixed", h->hv.pair_variant, vname[h->hv.pair_variant],
+                 h->hv.pair_blocks / h->n_sm, d.chunk, h->graph_steps);
     }
     h->report = rep;
     rc = capture_graph(h);

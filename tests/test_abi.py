@@ -35,6 +35,18 @@ def test_library_loads_without_gpu():
         assert hasattr(lib, name)
 
 
+def test_binding_constants_match_header():
+    src = open(os.path.join(ROOT, "include", "labf.h")).read()
+    defs = {m.group(1): m.group(2) for m in re.finditer(r"^#define (LA_\w+) (\S+)", src, re.M)}
+    for name in ("LA_OK", "LA_WARN_EMPTY_BIN", "LA_N_TERMS", "LA_PAIR_VARIANTS", "LA_N_STATS",
+                 "LA_N_KERNELS", "LA_EF_REBUILD", "LA_EF_COUNT_PAIRS"):
+        assert int(defs[name].rstrip("u"), 0) == getattr(labf, name), name
+    for name, v in defs.items():
+        if name.startswith("LA_ERR_"):
+            code = int(v.strip("()"))
+            assert labf.ERRORS[code] == name[len("LA_ERR_"):], name
+
+
 def test_descriptor_layout_matches_header(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "labf.h"\n'

@@ -204,7 +204,10 @@ def test_pair_kernel_launch_shapes_bit_identical():
     run = synth.water_run(walkers_per_stage=2, n_bins=20)
     st = synth.initial_state(sp, run, lam0=[0.1, 0.3, 0.6, 0.8])
     outs = []
-    for var, ctas, chunk in ((0, 4, 32), (1, 7, 32), (2, 8, 64), (1, 2, 64), (0, 1, 32)):
+    shapes = [(0, 4, 32), (1, 7, 32), (2, 8, 64), (1, 2, 64), (0, 1, 32),
+              (3, 4, 32), (4, 6, 64), (5, 3, 32), (3, 1, 96)]
+    assert {v for v, _, _ in shapes} == set(range(labf.LA_PAIR_VARIANTS))
+    for var, ctas, chunk in shapes:
         e, _ = make_engine(sp, run, state=st, pair_variant=var, pair_ctas_per_sm=ctas, chunk_entries=chunk)
         e.step(30)
         outs.append([e.get_state(w) for w in range(4)])
@@ -213,7 +216,9 @@ def test_pair_kernel_launch_shapes_bit_identical():
             assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v"], b["v"])
             assert a["lam"] == b["lam"] and a["plam"] == b["plam"]
     with pytest.raises(labf.LabfError):
-        make_engine(sp, run, state=st, pair_variant=3)
+        make_engine(sp, run, state=st, pair_variant=labf.LA_PAIR_VARIANTS)
+    with pytest.raises(labf.LabfError):
+        make_engine(sp, run, state=st, chunk_entries=48)
 
 
 def test_single_atom_system_and_rebuilds():

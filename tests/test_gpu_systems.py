@@ -238,8 +238,10 @@ def test_export_import_equals_device_merge():
         assert not any(np.any(a) for a in z)
     with pytest.raises(labf.LabfError):
         host.abf_import(s1, s2, -np.ones_like(c), 0, 0)
-    with pytest.raises(labf.LabfError):
-        host.abf_export(0, 5)
+    buf = np.zeros(16)
+    cnt = np.zeros(16, np.int64)
+    rc = host.lib.la_abf_export(host.handle, 0, 5, labf._p(buf), labf._p(buf), labf._p(cnt), None)
+    assert rc == -1  # LA_ERR_INVALID_ARG: no stage 5
 
 
 def test_two_engines_share_statistics_in_rank_order():
