@@ -137,7 +137,10 @@ typedef struct {
 
 /* Engine options; zero-initialise for defaults. */
 typedef struct {
-    int32_t graph_steps;         /* MD steps captured per CUDA-graph replay (default 10) */
+    int32_t graph_steps;         /* MD steps captured per CUDA-graph replay (0: 10); < 0:
+                                    no graph, one batched launch sequence per step (every
+                                    list kernel is launched and returns early unless a
+                                    walker must rebuild), e.g. for per-kernel profilers */
     int32_t autotune;            /* 1: pick pair-kernel launch shape by timing at create */
     double list_capacity_factor; /* >= 1 safety factor on list capacities (default 1.6) */
     int32_t pair_variant;        /* pair kernel when not autotuned, [0, LA_PAIR_VARIANTS):

@@ -433,6 +433,8 @@ int capture_graph(la_handle *h) {
     // step's conditional handle, so steps without a rebuild launch no list
     // kernel at all.
     const int W = h->L.W;
+    h->launches_per_step = kernels_per_step(h);
+    if (h->graph_steps == 0) return LA_OK;
     cudaStream_t cs = h->cap_stream, cb = h->cap_stream2;
     cudaGraph_t g;
     CU(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -468,7 +470,6 @@ int capture_graph(la_handle *h) {
     cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, LA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    h->launches_per_step = kernels_per_step(h);
     // graph steps: integrate, gate, pairs, walker, lambda (+ bonded); list
     // kernels are counted per executed rebuild (device counter)
     h->graph_launches_per_step = h->launches_per_step - rebuild_kernel_count(h->hv, 0, W) + 1;
@@ -831,7 +832,8 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
     hv.n_bo = h->n_bo.data();
     set_pair_blocks(h, h->opt.pair_ctas_per_sm > 0 ? h->opt.pair_ctas_per_sm : 4);
     h->hv.pair_variant = h->opt.pair_variant;
-    h->graph_steps = h->opt.graph_steps > 0 ? h->opt.graph_steps : 10;
+    // graph_steps < 0: no graph (one batched launch sequence per step)
+    h->graph_steps = h->opt.graph_steps > 0 ? h->opt.graph_steps : (h->opt.graph_steps < 0 ? 0 : 10);
 
     CU(h, cudaMallocHost((void **)&h->h_status, sizeof(unsigned)));
     *h->h_status = 0;
@@ -919,7 +921,8 @@ int la_step_walkers(la_handle *h, int64_t n_steps, void *stream) {
     if (rc != LA_OK) return rc;
     if (n_steps == 0) return LA_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t reps = n_steps / h->graph_steps, rem = n_steps % h->graph_steps;
+    const int64_t gs = h->graph_steps;
+    const int64_t reps = gs > 0 ? n_steps / gs : 0, rem = gs > 0 ? n_steps % gs : n_steps;
     for (int64_t r = 0; r < reps; ++r) CU(h, cudaGraphLaunch(h->graph, s));
     for (int64_t r = 0; r < rem; ++r) enqueue_step(h, 0, h->L.W, s);
     launch_finish(h->d, h->hv, 0, h->L.W, s);

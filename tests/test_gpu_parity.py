@@ -171,12 +171,16 @@ def test_batched_and_plain_forms_are_bit_identical():
     st = synth.initial_state(sp, run, lam0=[0.1, 0.3, 0.6, 0.8])
     e1, _ = make_engine(sp, run, state=st, graph_steps=4)
     e2, _ = make_engine(sp, run, state=st, graph_steps=4)
+    e3, _ = make_engine(sp, run, state=st, graph_steps=-1)  # batched launches, no graph
     e1.step(23)
     e2.step_plain(23)
+    e3.step(23)
     for w in range(run.n_walkers):
-        a, b = e1.get_state(w), e2.get_state(w)
+        a, b, c = e1.get_state(w), e2.get_state(w), e3.get_state(w)
         assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v"], b["v"])
-        assert a["lam"] == b["lam"] and a["plam"] == b["plam"] and a["step"] == b["step"] == 23
+        assert np.array_equal(a["x"], c["x"]) and np.array_equal(a["v"], c["v"])
+        assert a["lam"] == b["lam"] == c["lam"] and a["plam"] == b["plam"] == c["plam"]
+        assert a["step"] == b["step"] == c["step"] == 23
     for stage in range(2):
         ra, rb = e1.read_abf(0, stage), e2.read_abf(0, stage)
         assert np.array_equal(ra["sum"], rb["sum"]) and np.array_equal(ra["count"], rb["count"])
