@@ -324,6 +324,10 @@ __device__ __forceinline__ bool excluded_meta(int a, int2 ma, int4 ea, int b, in
 
 constexpr int LB_WARPS = 4;
 
+// work items (S, k) are handed out by a global counter (counters[8]); the
+// last warp out (counters[9]) resets both for the next launch
+constexpr int CTR_LB_ITEM = 8, CTR_LB_DONE = 9;
+
 __global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int w1) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int ia = lane & 7, jb = lane >> 3;
@@ -331,10 +335,13 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int 
     __shared__ int2 s_m[LB_WARPS][SC], t_m[LB_WARPS][SC];
     __shared__ int4 s_e[LB_WARPS][SC], t_e[LB_WARPS][SC];
     __shared__ int4 s_bb[LB_WARPS][2 * NIC + 2], t_bb[LB_WARPS][2 * NJC];
-    const long long nwarp = (long long)gridDim.x * LB_WARPS;
     const int s_begin = d.walk[w0].sc_off, s_end = d.walk[w1 - 1].sc_off + d.walk[w1 - 1].sc_cap;
     const long long total = (long long)(s_end - s_begin) * d.ncs;
-    for (long long idx = (long long)blockIdx.x * LB_WARPS + wib; idx < total; idx += nwarp) {
+    for (;;) {
+        long long idx = 0;
+        if (lane == 0) idx = (long long)atomicAdd(&d.counters[CTR_LB_ITEM], 1ull);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= total) break;
         const int s = s_begin + (int)(idx / d.ncs), kslot = (int)(idx % d.ncs);
         int lo = w0, hi = w1 - 1;
         while (lo < hi) {
@@ -348,6 +355,10 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int 
         const int S_loc = s - W.sc_off;
         const int nsc = d.n_sc[w];
         const size_t sub = (size_t)s * d.ncs + kslot;
+        if (S_loc >= nsc || kslot >= S.cspan * S.cspan) {
+            if (lane == 0) d.sub_n[sub] = 0;
+            continue;
+        }
         const int4 slo = d.bb_sc[2 * (size_t)s], shi = d.bb_sc[2 * (size_t)s + 1];
         const int ncx = S.ncx;
         const int cx0 = (int)(((long long)(slo.x - S.Rq) * ncx) >> 24);
@@ -355,7 +366,7 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int 
         const int cy0 = (int)(((long long)(slo.y - S.Rq) * ncx) >> 24);
         const int cy1 = (int)(((long long)(shi.y + S.Rq) * ncx) >> 24);
         const int cx = cx0 + kslot % S.cspan, cy = cy0 + kslot / S.cspan;
-        if (S_loc >= nsc || kslot >= S.cspan * S.cspan || cx > cx1 || cy > cy1) {
+        if (cx > cx1 || cy > cy1) {
             if (lane == 0) d.sub_n[sub] = 0;
             continue;
         }
@@ -408,29 +419,42 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int 
                 const int shx = tx * U, shy = ty * U, shz = tz * U;
                 const bool self0 = (T_loc == S_loc) && tx == 0 && ty == 0 && tz == 0;
                 const int shift_bits = (tx + 1) | ((ty + 1) << 2) | ((tz + 1) << 4);
-                unsigned cm[4];  // lane-parallel box tests of the 128 (jc, ic) combinations
+                // lane-parallel box tests of the 128 (jc, ic) combinations:
+                // bit (jc & 3) * 8 + ic of word jc >> 2
+                unsigned cm0, cm1, cm2, cm3;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int c = lane + 32 * q, jc = c >> 3, ic = c & 7;
                     const int4 jlo = t_bb[wib][2 * jc], jhi = t_bb[wib][2 * jc + 1];
                     const int4 ilo = s_bb[wib][2 * ic], ihi = s_bb[wib][2 * ic + 1];
                     const bool ok = jlo.w > 0 && ilo.w > 0 && bb_dist2(ilo, ihi, jlo, jhi, shx, shy, shz) < R;
-                    cm[q] = __ballot_sync(0xffffffffu, ok);
+                    const unsigned b = __ballot_sync(0xffffffffu, ok);
+                    if (q == 0) cm0 = b; else if (q == 1) cm1 = b; else if (q == 2) cm2 = b; else cm3 = b;
                 }
-                for (int jc = 0; jc < NJC; ++jc) {
-                    const unsigned cand = (cm[jc >> 2] >> ((jc & 3) * 8)) & 0xffu;
-                    if (!cand) continue;
+                // j-clusters with at least one candidate i-cluster, ascending
+                unsigned jmask = 0;
+#pragma unroll
+                for (int t4 = 0; t4 < 4; ++t4) {
+                    jmask |= ((cm0 >> (8 * t4)) & 0xffu) ? 1u << t4 : 0u;
+                    jmask |= ((cm1 >> (8 * t4)) & 0xffu) ? 1u << (4 + t4) : 0u;
+                    jmask |= ((cm2 >> (8 * t4)) & 0xffu) ? 1u << (8 + t4) : 0u;
+                    jmask |= ((cm3 >> (8 * t4)) & 0xffu) ? 1u << (12 + t4) : 0u;
+                }
+                for (; jmask; jmask &= jmask - 1u) {
+                    const int jc = __ffs(jmask) - 1;
+                    const unsigned cw = jc < 8 ? (jc < 4 ? cm0 : cm1) : (jc < 12 ? cm2 : cm3);
+                    const unsigned cand = (cw >> ((jc & 3) * 8)) & 0xffu;
                     const int4 uj = t_u[wib][jc * JC + jb];
                     const int2 mj = t_m[wib][jc * JC + jb];
                     const int4 ej = t_e[wib][jc * JC + jb];
+                    const bool jvalid = uj.w >= 0 && !mj.y;
                     unsigned lbyte = 0, imask = 0;
-#pragma unroll
-                    for (int ic = 0; ic < NIC; ++ic) {
-                        if (!(cand & (1u << ic))) continue;
+                    for (unsigned m = cand; m; m &= m - 1u) {  // candidate i-clusters, ascending
+                        const int ic = __ffs(m) - 1;
                         const int si = ic * IC + ia;
                         const int4 ui = s_u[wib][si];
                         const int2 mi = s_m[wib][si];
-                        bool ok = ui.w >= 0 && uj.w >= 0 && !mi.y && !mj.y;
+                        bool ok = jvalid && ui.w >= 0 && !mi.y;
                         if (self0) ok = ok && si < jc * JC + jb;
                         // D < R implies every component lies in (-2^23, 2^23) (R <= 2^46
                         // because L >= 2 r_list), i.e. this shift is the minimum image
@@ -460,6 +484,16 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int 
         }
         if (lane == 0) d.sub_n[sub] = min(nent, d.sub_cap);
         __syncwarp();
+    }
+    // the last warp out resets the work counters for the next launch
+    if (lane == 0) {
+        __threadfence();
+        const unsigned long long done = atomicAdd(&d.counters[CTR_LB_DONE], 1ull);
+        if (done == (unsigned long long)gridDim.x * LB_WARPS - 1ull) {
+            d.counters[CTR_LB_ITEM] = 0ull;
+            d.counters[CTR_LB_DONE] = 0ull;
+            __threadfence();
+        }
     }
 }
 
@@ -684,7 +718,7 @@ void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream
     k_permute_scatter<<<sb, 256, 0, s>>>(d, g0, g1);
     {
         long long nlb = ((long long)nsc * hv.ncs + LB_WARPS - 1) / LB_WARPS;
-        int lb = (int)(nlb < (long long)hv.n_sm * 32 ? nlb : (long long)hv.n_sm * 32);
+        int lb = (int)(nlb < (long long)hv.n_sm * 6 ? nlb : (long long)hv.n_sm * 6);  // resident grid
         k_listbuild<<<lb < 1 ? 1 : lb, LB_WARPS * 32, 0, s>>>(d, w0, w1);
         k_listcompact<<<kb, 128, 0, s>>>(d, w0, w1);
     }

@@ -558,8 +558,11 @@ __device__ __forceinline__ void alch_items(const Dev &d, int w0, int w1, int a0,
 template <bool ENERGY, int WARPS, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(Dev d, int w0, int w1, int nblk_pairs, int a0, int a1) {
     __shared__ PairShared<WARPS> sh;
-    if (blockIdx.x >= nblk_pairs) {
-        alch_items<ENERGY, WARPS>(d, w0, w1, a0, a1, blockIdx.x - nblk_pairs, gridDim.x - nblk_pairs);
+    // the alchemical blocks come first, so that they run alongside the
+    // normal pairs instead of after them
+    const int nblk_alch = gridDim.x - nblk_pairs;
+    if ((int)blockIdx.x < nblk_alch) {
+        alch_items<ENERGY, WARPS>(d, w0, w1, a0, a1, blockIdx.x, nblk_alch);
         return;
     }
     if (threadIdx.x == 0) {
@@ -577,8 +580,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(Dev d, int w0, int w
 template <int WARPS, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_x2(Dev d, int w0, int w1, int nblk_pairs, int a0, int a1) {
     __shared__ PairShared2<WARPS> sh;
-    if (blockIdx.x >= nblk_pairs) {
-        alch_items<false, WARPS>(d, w0, w1, a0, a1, blockIdx.x - nblk_pairs, gridDim.x - nblk_pairs);
+    const int nblk_alch = gridDim.x - nblk_pairs;
+    if ((int)blockIdx.x < nblk_alch) {
+        alch_items<false, WARPS>(d, w0, w1, a0, a1, blockIdx.x, nblk_alch);
         return;
     }
     if (threadIdx.x == 0) {

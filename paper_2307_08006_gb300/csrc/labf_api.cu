@@ -280,7 +280,7 @@ size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io
     d.th_d = a.take<double>((size_t)L.total_bins * L.P_max);
     d.th_sd = a.take<double>((size_t)L.total_bins * L.P_max);
     d.status = a.take<unsigned int>(4);
-    d.counters = a.take<unsigned long long>(8);
+    d.counters = a.take<unsigned long long>(16);
     const int iof = std::max(IO_FLOATS_MIN, 8 * L.max_n);
     *io = a.take<float>(iof);
     *io_floats = iof;

@@ -161,7 +161,8 @@ struct Dev {
     double *th_d2, *th_d, *th_sd;
     // status and counters
     unsigned int *status;
-    unsigned long long *counters; // [0] rebuilds [1] pairs normal [2] pairs alch
+    unsigned long long *counters; // [0] rebuilds [1] pairs normal [2] pairs alch [4, 5] pair
+                                  // work items [6] rebuild events [8, 9] list-build work items
 };
 
 // ---------------------------------------------------------------------------
