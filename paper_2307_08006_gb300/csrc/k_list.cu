@@ -38,7 +38,16 @@ __global__ void k_quantize(Dev d, int g0, int g1) {
         const int c = cx + S.ncx * cy;
         d.t_uq[g] = make_int4((int)ux, (int)uy, (int)uz, a);
         d.t_col[g] = c;
-        d.t_pos[g] = atomicAdd(&d.col_count[W.col_off + c], 1);
+        // one atomic per (walker, column) group of the warp's active lanes
+        // (slots of a warp are spatially sorted, so most lanes share one)
+        const int key = W.col_off + c;
+        const unsigned grp = __match_any_sync(__activemask(), key);
+        const int leader = __ffs(grp) - 1;
+        const int lane = threadIdx.x & 31;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&d.col_count[key], __popc(grp));
+        base = __shfl_sync(grp, base, leader);
+        d.t_pos[g] = base + __popc(grp & ((1u << lane) - 1u));
     }
 }
 
@@ -328,7 +337,7 @@ constexpr int LB_WARPS = 4;
 // last warp out (counters[9]) resets both for the next launch
 constexpr int CTR_LB_ITEM = 8, CTR_LB_DONE = 9;
 
-__global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int w1) {
+__global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, int w1) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int ia = lane & 7, jb = lane >> 3;
     __shared__ int4 s_u[LB_WARPS][SC], t_u[LB_WARPS][SC];
@@ -374,9 +383,14 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int 
             set_status(d, LA_STATUS_LIST_OVERFLOW);  // cannot happen for boxes inside a column
         const int gS = W.slot_off + S_loc * SC;
         __syncwarp();
+        // staged .w: the atom id, or -1 for a slot without normal pairs
+        // (padding or alchemical)
         for (int k = lane; k < SC; k += 32) {
-            s_u[wib][k] = d.uq[gS + k];
-            s_m[wib][k] = d.smeta[gS + k];
+            int4 u = d.uq[gS + k];
+            const int2 m = d.smeta[gS + k];
+            if (m.y) u.w = -1;
+            s_u[wib][k] = u;
+            s_m[wib][k] = m;
             s_e[wib][k] = d.sexcl[gS + k];
         }
         if (lane < 2 * NIC) s_bb[wib][lane] = d.bb_ic[2 * (size_t)s * NIC + lane];
@@ -408,8 +422,11 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int 
             const int gT = W.slot_off + T_loc * SC;
             __syncwarp();
             for (int k = lane; k < SC; k += 32) {
-                t_u[wib][k] = d.uq[gT + k];
-                t_m[wib][k] = d.smeta[gT + k];
+                int4 u = d.uq[gT + k];
+                const int2 m = d.smeta[gT + k];
+                if (m.y) u.w = -1;
+                t_u[wib][k] = u;
+                t_m[wib][k] = m;
                 t_e[wib][k] = d.sexcl[gT + k];
             }
             t_bb[wib][lane] = d.bb_jc[2 * (size_t)t * NJC + lane];
@@ -447,14 +464,12 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int 
                     const int4 uj = t_u[wib][jc * JC + jb];
                     const int2 mj = t_m[wib][jc * JC + jb];
                     const int4 ej = t_e[wib][jc * JC + jb];
-                    const bool jvalid = uj.w >= 0 && !mj.y;
                     unsigned lbyte = 0, imask = 0;
                     for (unsigned m = cand; m; m &= m - 1u) {  // candidate i-clusters, ascending
                         const int ic = __ffs(m) - 1;
                         const int si = ic * IC + ia;
                         const int4 ui = s_u[wib][si];
-                        const int2 mi = s_m[wib][si];
-                        bool ok = jvalid && ui.w >= 0 && !mi.y;
+                        bool ok = (ui.w | uj.w) >= 0;
                         if (self0) ok = ok && si < jc * JC + jb;
                         // D < R implies every component lies in (-2^23, 2^23) (R <= 2^46
                         // because L >= 2 r_list), i.e. this shift is the minimum image
@@ -462,6 +477,7 @@ __global__ void __launch_bounds__(LB_WARPS * 32) k_listbuild(Dev d, int w0, int 
                         ok = ok && (long long)dx * dx + (long long)dy * dy + (long long)dz * dz < R;
                         if (ok) {
                             const int4 ei = s_e[wib][si];
+                            const int2 mi = s_m[wib][si];
                             if (mi.x >= 0 && mi.x == mj.x) ok = false;
                             else if ((ei.x & ei.y & ei.z & ei.w & ej.x & ej.y & ej.z & ej.w) != -1)
                                 ok = !excluded_meta(ui.w, mi, ei, uj.w, mj, ej);  // some partner list is not empty
@@ -531,15 +547,20 @@ __global__ void k_listcompact(Dev d, int w0, int w1) {
 }
 
 // -------------------------------------------------------------------------
-// R9: alchemical list: one warp per (walker, alchemical atom).  Super-cluster
-// boxes are tested lane-parallel; the slots of the boxes in range are then
-// tested exactly, four slots per lane per pass, in super-cluster and slot
-// order (deterministic output order).
+// R9: alchemical list: one block per (walker, alchemical atom).  Super-cluster
+// boxes are tested lane-parallel; the 64 slots of each box in range are then
+// tested exactly (two per lane) by the block's warps in turn, and the hits
+// are written in super-cluster and slot order (deterministic output order).
 // -------------------------------------------------------------------------
-__global__ void k_alchlist(Dev d, int w0, int w1, int a0, int a1) {
-    const int lane = threadIdx.x & 31;
-    const int nwarp = gridDim.x * (blockDim.x >> 5);
-    for (int it = a0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < a1; it += nwarp) {
+constexpr int AL_WARPS = 4;
+
+__global__ void __launch_bounds__(AL_WARPS * 32) k_alchlist(Dev d, int w0, int w1, int a0, int a1) {
+    // one block per (walker, alchemical atom); the near super-clusters of
+    // each chunk of 32 are tested by the block's warps in turn, and warp 0
+    // writes the hits in (super-cluster, slot) order
+    __shared__ unsigned long long okm[32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int it = a0 + blockIdx.x; it < a1; it += gridDim.x) {
         int lo = w0, hi = w1 - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
@@ -580,38 +601,51 @@ __global__ void k_alchlist(Dev d, int w0, int w1, int a0, int a1) {
                     near = D < S.R;
                 }
             }
-            unsigned nm = __ballot_sync(0xffffffffu, near);
-            while (nm) {
-                const int k = __ffs(nm) - 1;
-                nm &= nm - 1;
-                const int gbase = W.slot_off + (b0 + k) * SC;
-                bool ok[2];
+            const unsigned nm = __ballot_sync(0xffffffffu, near);
+            int kk = 0;
+            for (unsigned m = nm; m; m &= m - 1u, ++kk) {
+                if ((kk % AL_WARPS) != wib) continue;
+                const int gbase = W.slot_off + (b0 + __ffs(m) - 1) * SC;
+                unsigned bits[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int g = gbase + lane + 32 * h;
                     const int4 ub = d.uq[g];
                     const int2 mb = d.smeta[g];
-                    ok[h] = false;
+                    bool ok = false;
                     if (ub.w >= 0 && !mb.y) {
                         const long long dx = torus_delta(ub.x, ua.x), dy = torus_delta(ub.y, ua.y),
                                         dz = torus_delta(ub.z, ua.z);
-                        ok[h] = dx * dx + dy * dy + dz * dz < S.R && !excluded_meta(a, ma, ea, ub.w, mb, d.sexcl[g]);
+                        ok = dx * dx + dy * dy + dz * dz < S.R && !excluded_meta(a, ma, ea, ub.w, mb, d.sexcl[g]);
+                    }
+                    bits[h] = __ballot_sync(0xffffffffu, ok);
+                }
+                if (lane == 0) okm[kk] = ((unsigned long long)bits[1] << 32) | bits[0];
+            }
+            __syncthreads();
+            if (wib == 0) {
+                kk = 0;
+                for (unsigned m = nm; m; m &= m - 1u, ++kk) {
+                    const int gbase = W.slot_off + (b0 + __ffs(m) - 1) * SC;
+                    const unsigned long long om = okm[kk];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const unsigned mh = h ? (unsigned)(om >> 32) : (unsigned)om;
+                        const int pos = cnt + __popc(mh & ((1u << lane) - 1u));
+                        if (((mh >> lane) & 1u) && pos < d.alch_cap) out[pos] = gbase + lane + 32 * h;
+                        cnt += __popc(mh);
                     }
                 }
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const unsigned m = __ballot_sync(0xffffffffu, ok[h]);
-                    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-                    if (ok[h] && pos < d.alch_cap) out[pos] = gbase + lane + 32 * h;
-                    cnt += __popc(m);
-                }
             }
+            __syncthreads();
         }
-        if (cnt > d.alch_cap) {
-            if (lane == 0) set_status(d, LA_STATUS_ALCH_OVERFLOW);
-            cnt = d.alch_cap;
+        if (wib == 0) {
+            if (cnt > d.alch_cap) {
+                if (lane == 0) set_status(d, LA_STATUS_ALCH_OVERFLOW);
+                cnt = d.alch_cap;
+            }
+            if (lane == 0) d.alch_cnt[it] = cnt;
         }
-        if (lane == 0) d.alch_cnt[it] = cnt;
     }
 }
 
@@ -718,14 +752,14 @@ void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream
     k_permute_scatter<<<sb, 256, 0, s>>>(d, g0, g1);
     {
         long long nlb = ((long long)nsc * hv.ncs + LB_WARPS - 1) / LB_WARPS;
-        int lb = (int)(nlb < (long long)hv.n_sm * 6 ? nlb : (long long)hv.n_sm * 6);  // resident grid
+        int lb = (int)(nlb < (long long)hv.n_sm * 8 ? nlb : (long long)hv.n_sm * 8);  // resident grid
         k_listbuild<<<lb < 1 ? 1 : lb, LB_WARPS * 32, 0, s>>>(d, w0, w1);
         k_listcompact<<<kb, 128, 0, s>>>(d, w0, w1);
     }
     if (a1 > a0) {
-        int ab = (a1 - a0 + 3) / 4;
+        int ab = a1 - a0;
         ab = ab > hv.n_sm * 8 ? hv.n_sm * 8 : ab;
-        k_alchlist<<<ab, 128, 0, s>>>(d, w0, w1, a0, a1);
+        k_alchlist<<<ab, AL_WARPS * 32, 0, s>>>(d, w0, w1, a0, a1);
     }
     k_items<<<nw, 256, 0, s>>>(d, w0);
 }
