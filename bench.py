@@ -143,6 +143,30 @@ class ClockSampler:
                     reasons=reasons, samples=len(rows))
 
 
+def measured_traffic(variant):
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, or
+    None when that capture is of another variant or of older kernel source."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "k_pairs_solvation16.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, "no capture"
+    m = re.search(r"traffic_bytes_per_launch: variant=(\d+) dram_read=(\d+) dram_write=(\d+) "
+                  r"source_sha256=(\w+)", text)
+    if not m:
+        return None, "no capture"
+    h = hashlib.sha256()
+    for f in ("k_pairs.cu", "labf_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2307_08006_gb300", "csrc", f), "rb").read())
+    if h.hexdigest()[:16] != m.group(4):
+        return None, "kernel source changed since the capture"
+    if int(m.group(1)) != variant:
+        return None, f"capture is of pair_variant={m.group(1)}"
+    return int(m.group(2)) + int(m.group(3)), "profiles/k_pairs_solvation16.md (ncu, one launch)"
+
+
 def flush_l2(buf):
     buf.add_(1)  # 256 MB read + write, larger than the 129 MB L2
 
@@ -289,6 +313,8 @@ def gpu_arm(args):
     eng.sync()
     csum = clk.summary(local)
 
+    m = re.search(r"pair_variant=(\d+)", eng.autotune_report())
+    traffic, traffic_src = measured_traffic(int(m.group(1)) if m else -1)
     if rank == 0:
         cb = None
         if world == 1 and not args.no_cpu_baseline:
@@ -316,7 +342,7 @@ def gpu_arm(args):
                           "host<->device copies in the timed region"),
             gpu_launches=launches,
             roofline=dict(bound="alu", achieved=achieved, peak=peak_tflops, unit="TFLOP/s",
-                          frac=achieved / peak_tflops, traffic=None,
+                          frac=achieved / peak_tflops, traffic=traffic, traffic_source=traffic_src,
                           kernel="k_pairs (normal + alchemical pairs)",
                           pair_kernel_ms=pair_ms,
                           peak_note=f"{n_sm} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
