@@ -333,6 +333,18 @@ int la_stats(la_handle *h, int64_t *out, void *stream);
 #define LA_N_KERNELS 6 /* integrate, rebuild (all list kernels), pairs, bonded, walker, lambda */
 int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_out, void *stream);
 
+/*
+ * la_autotune: choose the pair kernel's launch shape (variant, grid, work-item
+ * size) by timing repeated pair-kernel launches on the current neighbour
+ * lists, e.g. after equilibration, when the lists differ from those of the
+ * starting structure.  The state does not change: forces are restored bit
+ * for bit afterwards, and every shape gives identical results.  The CUDA
+ * graph is re-captured.  la_create_system with autotune = 1 does the same
+ * at creation (reusing an earlier result for the same system shape).
+ * Synchronising.
+ */
+int la_autotune(la_handle *h, void *stream);
+
 /* la_autotune_report: text describing the chosen launch shapes (static buffer). */
 const char *la_autotune_report(la_handle *h);
 

@@ -764,6 +764,10 @@ void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream
     k_items<<<nw, 256, 0, s>>>(d, w0);
 }
 
+void launch_items(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s) {
+    k_items<<<w1 - w0, 256, 0, s>>>(d, w0);
+}
+
 int rebuild_kernel_count(const HostView &hv, int w0, int w1) {
     const int a0 = hv.alch_base[w0], a1 = hv.alch_base[w1 - 1] + hv.n_alch[w1 - 1];
     return a1 > a0 ? 11 : 10;

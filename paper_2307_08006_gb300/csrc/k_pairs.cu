@@ -35,6 +35,7 @@
 // s = alpha (1 - lambda_v)^m + (r/sigma)^6, RF scaled by lambda_e; per-lane
 // FP64 sums of dU/dlambda_v, dU/dlambda_e, energies and theta derivatives,
 // reduced with a fixed shuffle tree (deterministic).
+#include "labf_dyn.cuh"
 #include "labf_internal.cuh"
 #include "labf_launch.h"
 
@@ -433,11 +434,45 @@ __device__ __forceinline__ void normal_items_x2(const Dev &d, int w0, int w1, in
     }
 }
 
-template <bool ENERGY, int WARPS>
+// Fused launch: a walker's terms (walker_work) need all its alchemical
+// items, and a stage's lambda update (lambda_work) needs all its walkers.
+// Each finished item, plus one extra trigger item per walker, arrives on
+// the walker's counter; the warp that arrives last does the walker's work and
+// arrives on the stage's counter, whose last arrival does the stage's work.
+// Writers fence before arriving; counters are reset by the last arrival.
+// No warp waits for another.
+__device__ __forceinline__ void arrive_walker(const Dev &d, int w, int lane) {
+    __threadfence();
+    unsigned old = 0;
+    if (lane == 0) old = atomicAdd(&d.wdone[w], 1u);
+    old = __shfl_sync(FULL, old, 0);
+    const WalkerDev &W = d.walk[w];
+    if (old != (unsigned)d.sys[W.sys].n_alch) return;  // n_alch + 1 arrivals
+    if (lane == 0) d.wdone[w] = 0u;
+    __threadfence();
+    walker_work<false>(d, w, lane);
+    __threadfence();
+    const int si = W.stage;
+    const StageDev &st = d.stage[si];
+    unsigned old2 = 0;
+    if (lane == 0) old2 = atomicAdd(&d.sdone[si], 1u);
+    old2 = __shfl_sync(FULL, old2, 0);
+    if (old2 != (unsigned)(st.w1 - st.w0 - 1)) return;
+    if (lane == 0) d.sdone[si] = 0u;
+    __threadfence();
+    lambda_work<true>(d, si, 0, lane, 32);
+}
+
+template <bool ENERGY, int WARPS, bool FUSED>
 __device__ __forceinline__ void alch_items(const Dev &d, int w0, int w1, int a0, int a1, int blk, int nblk) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nwarps = nblk * WARPS;
-    for (int it = a0 + blk * WARPS + wib; it < a1; it += nwarps) {
+    const int aend = FUSED ? a1 + (w1 - w0) : a1;
+    for (int it = a0 + blk * WARPS + wib; it < aend; it += nwarps) {
+        if (FUSED && it >= a1) {  // trigger item of walker w0 + (it - a1)
+            arrive_walker(d, w0 + (it - a1), lane);
+            continue;
+        }
         int lo = w0, hi = w1 - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
@@ -548,21 +583,35 @@ __device__ __forceinline__ void alch_items(const Dev &d, int w0, int w1, int a0,
             }
             if (ENERGY) atomicAdd(&d.counters[2], (unsigned long long)npair);
         }
+        if (FUSED) arrive_walker(d, w, lane);
     }
+}
+
+// bonded terms in the fused launch: blocks [0, nblk) of the bonded range
+__device__ __forceinline__ void bonded_items(const Dev &d, int w0, int w1, int blk, int nblk) {
+    const int b0 = d.walk[w0].bo_off;
+    const int b1 = d.walk[w1 - 1].bo_off + d.walk[w1 - 1].n_bo;
+    const int nthr = nblk * blockDim.x;
+    for (int t = b0 + blk * blockDim.x + threadIdx.x; t < b1; t += nthr) bonded_term<false>(d, t, w0, w1);
 }
 
 // WARPS x 32 threads per CTA; MINB: resident CTAs per SM the register
 // allocation is sized for.  Variants (autotuned): scalar 8 warps / 3 CTAs (80
 // registers), 4 warps / 7 CTAs (72), 4 warps / 8 CTAs (64); packed 4 warps /
 // 6 CTAs (80), 4 warps / 5 CTAs (96), 8 warps / 3 CTAs (80).
-template <bool ENERGY, int WARPS, int MINB>
-__global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(Dev d, int w0, int w1, int nblk_pairs, int a0, int a1) {
+template <bool ENERGY, int WARPS, int MINB, bool FUSED>
+__global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(Dev d, int w0, int w1, int nblk_pairs, int a0, int a1,
+                                                          int nblk_bonded) {
     __shared__ PairShared<WARPS> sh;
-    // the alchemical blocks come first, so that they run alongside the
-    // normal pairs instead of after them
-    const int nblk_alch = gridDim.x - nblk_pairs;
+    // grid: [alchemical items][bonded terms][normal pairs]; the first two
+    // come first so that they run alongside the normal pairs
+    const int nblk_alch = gridDim.x - nblk_pairs - nblk_bonded;
     if ((int)blockIdx.x < nblk_alch) {
-        alch_items<ENERGY, WARPS>(d, w0, w1, a0, a1, blockIdx.x, nblk_alch);
+        alch_items<ENERGY, WARPS, FUSED>(d, w0, w1, a0, a1, blockIdx.x, nblk_alch);
+        return;
+    }
+    if (FUSED && (int)blockIdx.x < nblk_alch + nblk_bonded) {
+        bonded_items(d, w0, w1, blockIdx.x - nblk_alch, nblk_bonded);
         return;
     }
     if (threadIdx.x == 0) {
@@ -577,12 +626,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(Dev d, int w0, int w
     normal_items<ENERGY, WARPS>(d, w0, w1, nblk_pairs, sh);
 }
 
-template <int WARPS, int MINB>
-__global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_x2(Dev d, int w0, int w1, int nblk_pairs, int a0, int a1) {
+template <int WARPS, int MINB, bool FUSED>
+__global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_x2(Dev d, int w0, int w1, int nblk_pairs, int a0, int a1,
+                                                          int nblk_bonded) {
     __shared__ PairShared2<WARPS> sh;
-    const int nblk_alch = gridDim.x - nblk_pairs;
+    const int nblk_alch = gridDim.x - nblk_pairs - nblk_bonded;
     if ((int)blockIdx.x < nblk_alch) {
-        alch_items<false, WARPS>(d, w0, w1, a0, a1, blockIdx.x, nblk_alch);
+        alch_items<false, WARPS, FUSED>(d, w0, w1, a0, a1, blockIdx.x, nblk_alch);
+        return;
+    }
+    if (FUSED && (int)blockIdx.x < nblk_alch + nblk_bonded) {
+        bonded_items(d, w0, w1, blockIdx.x - nblk_alch, nblk_bonded);
         return;
     }
     if (threadIdx.x == 0) {
@@ -598,7 +652,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_x2(Dev d, int w0, in
 }
 
 template <bool ENERGY, int WARPS, int MINB, bool X2 = false>
-static void launch_pairs_v(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s) {
+static void launch_pairs_v(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s, bool fused = false) {
     int nblk = hv.pair_blocks * 8 / WARPS;  // pair_blocks counts 8-warp CTAs
     if (w1 - w0 < hv.n_walkers) {           // a subset of walkers: size the grid to its work
         int items = 0;
@@ -608,9 +662,32 @@ static void launch_pairs_v(const Dev &d, const HostView &hv, int w0, int w1, cud
         nblk = nblk < 1 ? 1 : nblk;
     }
     const int a0 = hv.alch_base[w0], a1 = hv.alch_base[w1 - 1] + hv.n_alch[w1 - 1];
-    const int ablk = (a1 - a0 + WARPS - 1) / WARPS;
-    if constexpr (X2) k_pairs_x2<WARPS, MINB><<<nblk + ablk, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1);
-    else k_pairs<ENERGY, WARPS, MINB><<<nblk + ablk, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1);
+    const int ablk = (a1 - a0 + (fused ? w1 - w0 : 0) + WARPS - 1) / WARPS;
+    int bblk = 0;
+    if (fused) {  // bonded terms: about four per thread
+        const int nbo = hv.bo_off[w1 - 1] + hv.n_bo[w1 - 1] - hv.bo_off[w0];
+        bblk = (nbo + 4 * WARPS * 32 - 1) / (4 * WARPS * 32);
+        bblk = bblk > hv.n_sm ? hv.n_sm : bblk;
+    }
+    const int grid = ablk + bblk + nblk;
+    if (fused) {
+        if constexpr (X2) k_pairs_x2<WARPS, MINB, true><<<grid, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1, bblk);
+        else k_pairs<ENERGY, WARPS, MINB, true><<<grid, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1, bblk);
+    } else {
+        if constexpr (X2) k_pairs_x2<WARPS, MINB, false><<<grid, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1, 0);
+        else k_pairs<ENERGY, WARPS, MINB, false><<<grid, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1, 0);
+    }
+}
+
+void launch_pairs_fused(const Dev &d, const HostView &hv, int n_stages, cudaStream_t s) {
+    const int W = hv.n_walkers;
+    (void)n_stages;
+    if (hv.pair_variant == 1) launch_pairs_v<false, 4, 7>(d, hv, 0, W, s, true);
+    else if (hv.pair_variant == 2) launch_pairs_v<false, 4, 8>(d, hv, 0, W, s, true);
+    else if (hv.pair_variant == 3) launch_pairs_v<false, 4, 6, true>(d, hv, 0, W, s, true);
+    else if (hv.pair_variant == 4) launch_pairs_v<false, 4, 5, true>(d, hv, 0, W, s, true);
+    else if (hv.pair_variant == 5) launch_pairs_v<false, 8, 3, true>(d, hv, 0, W, s, true);
+    else launch_pairs_v<false, 8, 3>(d, hv, 0, W, s, true);
 }
 
 void launch_pairs(const Dev &d, const HostView &hv, int w0, int w1, bool energy, cudaStream_t s) {

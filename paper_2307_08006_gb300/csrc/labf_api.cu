@@ -281,6 +281,8 @@ size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io
     d.th_sd = a.take<double>((size_t)L.total_bins * L.P_max);
     d.status = a.take<unsigned int>(4);
     d.counters = a.take<unsigned long long>(16);
+    d.wdone = a.take<unsigned int>(L.W);
+    d.sdone = a.take<unsigned int>(L.n_stages);
     const int iof = std::max(IO_FLOATS_MIN, 8 * L.max_n);
     *io = a.take<float>(iof);
     *io_floats = iof;
@@ -307,7 +309,7 @@ struct la_handle {
     cudaGraphExec_t graph = nullptr;
     cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
     long long graph_launches_per_step = 0;
-    int n_sm = 0;
+    int n_sm = 0, dev = 0;
     unsigned *h_status = nullptr;  // pinned
     cudaEvent_t status_ev = nullptr;
     int sticky = LA_OK;
@@ -384,22 +386,16 @@ int sync_status(la_handle *h, cudaStream_t s, unsigned *bits) {
 }
 
 // one batched MD step over walkers [w0, w1)
+// one batched MD step over all walkers: integrate, [rebuild], then one
+// launch for pairs, bonded terms, walker terms and the lambda update
 int enqueue_step(la_handle *h, int w0, int w1, cudaStream_t s) {
     launch_integrate(h->d, h->hv, w0, w1, s);
     launch_rebuild(h->d, h->hv, w0, w1, s);
-    launch_pairs(h->d, h->hv, w0, w1, false, s);
-    launch_bonded(h->d, h->hv, w0, w1, false, s);
-    launch_walker(h->d, w0, w1, false, s);
-    launch_lambda(h->d, 0, (int)h->stages.size(), false, s);
+    launch_pairs_fused(h->d, h->hv, (int)h->stages.size(), s);
     return 0;
 }
 
-int kernels_per_step(la_handle *h) {
-    int n = 1 + rebuild_kernel_count(h->hv, 0, h->L.W) + 1 + 1 + 1;
-    const int nbo = h->hv.bo_off[h->L.W - 1] + h->hv.n_bo[h->L.W - 1];
-    if (nbo > 0) ++n;
-    return n;
-}
+int kernels_per_step(la_handle *h) { return 1 + rebuild_kernel_count(h->hv, 0, h->L.W) + 1; }
 
 // evaluate forces, dU/dlambda and G at the current state of walkers [w0, w1)
 int prime(la_handle *h, int w0, int w1, bool force_rebuild, bool energy, cudaStream_t s) {
@@ -461,17 +457,14 @@ int capture_graph(la_handle *h) {
         cudaGraph_t body_out;
         CU(h, cudaStreamEndCapture(cb, &body_out));
         CU(h, cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
-        launch_pairs(h->d, h->hv, 0, W, false, cs);
-        launch_bonded(h->d, h->hv, 0, W, false, cs);
-        launch_walker(h->d, 0, W, false, cs);
-        launch_lambda(h->d, 0, (int)h->stages.size(), false, cs);
+        launch_pairs_fused(h->d, h->hv, (int)h->stages.size(), cs);
     }
     CU(h, cudaStreamEndCapture(cs, &g));
     cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, LA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    // graph steps: integrate, gate, pairs, walker, lambda (+ bonded); list
-    // kernels are counted per executed rebuild (device counter)
+    // graph steps: integrate, gate, fused pairs; list kernels are counted per
+    // executed rebuild (device counter)
     h->graph_launches_per_step = h->launches_per_step - rebuild_kernel_count(h->hv, 0, W) + 1;
     return LA_OK;
 }
@@ -480,24 +473,111 @@ void set_pair_blocks(la_handle *h, int ctas_per_sm) {
     h->hv.pair_blocks = std::max(1, ctas_per_sm) * h->n_sm;
 }
 
-int time_steps(la_handle *h, int n, cudaStream_t s, float *ms) {
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    cudaEventRecord(a, s);
-    for (int k = 0; k < n; ++k) enqueue_step(h, 0, h->L.W, s);
-    cudaEventRecord(b, s);
-    cudaError_t e = cudaEventSynchronize(b);
-    cudaEventElapsedTime(ms, a, b);
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    return e == cudaSuccess ? LA_OK : fail(h, LA_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
-}
-
-// autotuner results per (device, system shape): CTAs/SM, entries/item, register split
+// autotuner results per (device, system shape): CTAs/SM, entries/item, variant
 std::map<std::string, std::array<int, 3>> &tune_cache() {
     static std::map<std::string, std::array<int, 3>> c;
     return c;
+}
+
+// forces, dU/dlambda and G of every walker from the current lists (no
+// rebuild, no sample folded): bit-identical to what the last step left
+int refresh_forces(la_handle *h, cudaStream_t s) {
+    const int W = h->L.W;
+    const size_t g1 = (size_t)h->slot_off[W - 1] + h->slot_cap[W - 1];
+    CU(h, cudaMemsetAsync(h->d.F, 0, 3 * g1 * sizeof(unsigned long long), s));
+    launch_pairs(h->d, h->hv, 0, W, false, s);
+    launch_bonded(h->d, h->hv, 0, W, false, s);
+    launch_walker(h->d, 0, W, false, s);
+    launch_lambda(h->d, 0, (int)h->stages.size(), true, s);
+    CU(h, cudaGetLastError());
+    return LA_OK;
+}
+
+void make_report(la_handle *h) {
+    static const char *vname[LA_PAIR_VARIANTS] = {
+        "scalar, 8 warps/CTA, 80 registers", "scalar, 4 warps/CTA, 72 registers",
+        "scalar, 4 warps/CTA, 64 registers", "packed FP32x2, 4 warps/CTA, 80 registers",
+        "packed FP32x2, 4 warps/CTA, 96 registers", "packed FP32x2, 8 warps/CTA, 80 registers"};
+    char rep[512];
+    snprintf(rep, sizeof rep,
+             "%s: pair_variant=%d (%s), pair_ctas_per_sm=%d (8-warp CTA equivalents), "
+             "chunk_entries=%d, graph steps=%d",
+             h->opt.autotune ? "autotuned" : "fixed", h->hv.pair_variant, vname[h->hv.pair_variant],
+             h->hv.pair_blocks / h->n_sm, h->d.chunk, h->graph_steps);
+    h->report = rep;
+}
+
+// work items for the current chunk size from the current lists
+int rebuild_items(la_handle *h, cudaStream_t s) {
+    const int W = h->L.W;
+    unsigned long long nreb = 0;
+    CU(h, cudaMemcpyAsync(&nreb, h->d.counters, sizeof nreb, cudaMemcpyDeviceToHost, s));
+    std::vector<int> one(W, 1);
+    CU(h, cudaMemcpyAsync(h->d.rebuild, one.data(), sizeof(int) * W, cudaMemcpyHostToDevice, s));
+    launch_items(h->d, h->hv, 0, W, s);
+    CU(h, cudaMemcpyAsync(h->d.counters, &nreb, sizeof nreb, cudaMemcpyHostToDevice, s));  // not a rebuild
+    CU(h, cudaStreamSynchronize(s));
+    return LA_OK;
+}
+
+// Launch-shape tuner: times the pair kernel alone (repeated launches on the
+// current lists, nothing else changes) for every variant, grid size and
+// items size, keeps the fastest, then restores the forces exactly.
+int tune_pairs(la_handle *h, cudaStream_t s, bool use_cache) {
+    char key[256];
+    snprintf(key, sizeof key, "dev%d-sm%d-W%d-slots%lld-ent%d", h->dev, h->n_sm, h->L.W, h->L.slots,
+             h->L.ent_cap);
+    auto it = tune_cache().find(key);
+    int best_c = 4, best_k = h->L.chunk, best_m = 0;
+    if (use_cache && it != tune_cache().end()) {
+        best_c = it->second[0];
+        best_k = it->second[1];
+        best_m = it->second[2];
+    } else {
+        const int W = h->L.W;
+        float best = 1e30f;
+        const int ctas[] = {2, 3, 4, 6, 8};
+        const int chunksz[] = {32, 64};  // item capacity was sized for L.chunk
+        cudaEvent_t a, b;
+        CU(h, cudaEventCreate(&a));
+        CU(h, cudaEventCreate(&b));
+        for (int k : chunksz) {
+            if (k < h->L.chunk) continue;
+            h->d.chunk = k;
+            int rc = rebuild_items(h, s);
+            if (rc != LA_OK) return rc;
+            for (int m = 0; m < LA_PAIR_VARIANTS; ++m) {
+                h->hv.pair_variant = m;
+                for (int c : ctas) {
+                    set_pair_blocks(h, c);
+                    for (int r = 0; r < 2; ++r) launch_pairs(h->d, h->hv, 0, W, false, s);  // warm
+                    CU(h, cudaEventRecord(a, s));
+                    for (int r = 0; r < 10; ++r) launch_pairs(h->d, h->hv, 0, W, false, s);
+                    CU(h, cudaEventRecord(b, s));
+                    CU(h, cudaEventSynchronize(b));
+                    float ms = 0.f;
+                    CU(h, cudaEventElapsedTime(&ms, a, b));
+                    if (ms < best) {
+                        best = ms;
+                        best_c = c;
+                        best_k = k;
+                        best_m = m;
+                    }
+                }
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        tune_cache()[key] = {best_c, best_k, best_m};
+    }
+    h->hv.pair_variant = best_m;
+    set_pair_blocks(h, best_c);
+    if (h->d.chunk != best_k) {
+        h->d.chunk = best_k;
+        int rc = rebuild_items(h, s);
+        if (rc != LA_OK) return rc;
+    }
+    return refresh_forces(h, s);
 }
 
 }  // namespace
@@ -555,6 +635,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         return fail(h, LA_ERR_ARENA_TOO_SMALL, "arena of %zu bytes (need %zu, 256-byte aligned)", arena_bytes, need);
     int dev;
     CU(h, cudaGetDevice(&dev));
+    h->dev = dev;
     CU(h, cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
 
     Dev &d = h->d;
@@ -846,69 +927,14 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
     rc = sync_status(h, s, nullptr);
     if (rc != LA_OK) return rc;
 
-    // ---- launch-shape autotuner: CTAs per SM of the pair kernel, entries per item ----
-    char rep[512];
+    // ---- launch-shape autotuner (pair kernel only; the state does not move) ----
     if (h->opt.autotune) {
-        char key[256];
-        snprintf(key, sizeof key, "dev%d-sm%d-W%d-slots%lld-ent%d", dev, h->n_sm, L.W, L.slots, L.ent_cap);
-        auto it = tune_cache().find(key);
-        int best_c = 4, best_k = L.chunk, best_m = 0;
-        if (it != tune_cache().end()) {
-            best_c = it->second[0];
-            best_k = it->second[1];
-            best_m = it->second[2];
-        } else {
-            // timing advances the walkers: the initial state is re-loaded after
-            float best = 1e30f;
-            const int ctas[] = {2, 3, 4, 6, 8};
-            const int chunksz[] = {32, 64};  // item capacity was sized for L.chunk = 32
-            const int variants[] = {0, 1, 2, 3, 4, 5};
-            for (int m : variants) {
-                h->hv.pair_variant = m;
-                for (int k : chunksz) {
-                    if (k < L.chunk) continue;
-                    d.chunk = k;
-                    for (int c : ctas) {
-                        set_pair_blocks(h, c);
-                        rc = prime(h, 0, L.W, true, false, s);
-                        if (rc != LA_OK) return rc;
-                        float ms = 0.f;
-                        rc = time_steps(h, 2, s, &ms);  // warm
-                        if (rc != LA_OK) return rc;
-                        rc = time_steps(h, 6, s, &ms);
-                        if (rc != LA_OK) return rc;
-                        if (ms < best) {
-                            best = ms;
-                            best_c = c;
-                            best_k = k;
-                            best_m = m;
-                        }
-                    }
-                }
-            }
-            tune_cache()[key] = {best_c, best_k, best_m};
-        }
-        d.chunk = best_k;
-        h->hv.pair_variant = best_m;
-        set_pair_blocks(h, best_c);
-        rc = upload();
+        rc = tune_pairs(h, s, true);
         if (rc != LA_OK) return rc;
-        h->steps = 0;
-        rc = prime(h, 0, L.W, true, false, s);
+        rc = sync_status(h, s, nullptr);
         if (rc != LA_OK) return rc;
     }
-    {
-        static const char *vname[LA_PAIR_VARIANTS] = {
-            "scalar, 8 warps/CTA, 80 registers", "scalar, 4 warps/CTA, 72 registers",
-            "scalar, 4 warps/CTA, 64 registers", "packed FP32x2, 4 warps/CTA, 80 registers",
-            "packed FP32x2, 4 warps/CTA, 96 registers", "packed FP32x2, 8 warps/CTA, 80 registers"};
-        snprintf(rep, sizeof rep,
-                 "%s: pair_variant=%d (%s), pair_ctas_per_sm=%d (8-warp CTA equivalents), "
-                 "chunk_entries=%d, graph steps=%d",
-                 h->opt.autotune ? "autotuned" : "fixed", h->hv.pair_variant, vname[h->hv.pair_variant],
-                 h->hv.pair_blocks / h->n_sm, d.chunk, h->graph_steps);
-    }
-    h->report = rep;
+    make_report(h);
     rc = capture_graph(h);
     if (rc != LA_OK) return rc;
     return sync_status(h, s, nullptr);
@@ -1395,6 +1421,22 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
         ms_out[q] = (float)(acc[q] / n_steps);
         if (launches_out) launches_out[q] = cnt[q];
     }
+    return sync_status(h, s, nullptr);
+}
+
+int la_autotune(la_handle *h, void *stream) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    int rc = check_posted(h);
+    if (rc != LA_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = sync_status(h, s, nullptr);
+    if (rc != LA_OK) return rc;
+    rc = tune_pairs(h, s, false);
+    if (rc != LA_OK) return rc;
+    h->opt.autotune = 1;
+    make_report(h);
+    rc = capture_graph(h);
+    if (rc != LA_OK) return rc;
     return sync_status(h, s, nullptr);
 }
 

@@ -161,6 +161,7 @@ struct Dev {
     double *th_d2, *th_d, *th_sd;
     // status and counters
     unsigned int *status;
+    unsigned int *wdone, *sdone;  // arrivals per walker / per stage in the fused pair launch
     unsigned long long *counters; // [0] rebuilds [1] pairs normal [2] pairs alch [4, 5] pair
                                   // work items [6] rebuild events [8, 9] list-build work items
 };

@@ -33,7 +33,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "BOX_TOO_SMALL", -3: "CUDA", -4: "UNSUPPORTED",
 EXPORTED = ("la_query_sizes", "la_create_system", "la_step_walkers", "la_step_walkers_plain",
             "la_read_abf", "la_abf_export", "la_abf_import", "la_energy_forces", "la_get_state", "la_set_state", "la_set_alch_params",
             "la_read_theta", "la_get_pairs", "la_lambda_path", "la_sync", "la_stats",
-            "la_time_kernels", "la_autotune_report", "la_last_error", "la_destroy",
+            "la_time_kernels", "la_autotune", "la_autotune_report", "la_last_error", "la_destroy",
             "la_alch_pairs_static", "la_static_last_error")
 
 
@@ -115,6 +115,7 @@ def load(build_if_missing: bool = False):
     lib.la_sync.argtypes = [H, P, P]
     lib.la_stats.argtypes = [H, P, P]
     lib.la_time_kernels.argtypes = [H, I, P, P, P]
+    lib.la_autotune.argtypes = [H, P]
     lib.la_autotune_report.argtypes = [H]
     lib.la_autotune_report.restype = C.c_char_p
     lib.la_last_error.argtypes = [H]
@@ -393,6 +394,11 @@ class Engine:
         cnt = np.zeros(LA_N_KERNELS, np.int64)
         self._check(self.lib.la_time_kernels(self.handle, int(n_steps), _p(ms), _p(cnt), self._stream(stream)))
         return {k: (float(m), int(c)) for k, m, c in zip(KERNEL_NAMES, ms, cnt)}
+
+    def autotune(self, stream=None) -> str:
+        """Re-tune the pair kernel's launch shape on the current lists."""
+        self._check(self.lib.la_autotune(self.handle, self._stream(stream)))
+        return self.autotune_report()
 
     def autotune_report(self) -> str:
         return self.lib.la_autotune_report(self.handle).decode()

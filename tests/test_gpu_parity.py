@@ -225,6 +225,27 @@ def test_pair_kernel_launch_shapes_bit_identical():
         make_engine(sp, run, state=st, chunk_entries=48)
 
 
+def test_autotune_leaves_the_trajectory_unchanged():
+    sp = small_water(jitter=0.01)
+    run = synth.water_run(walkers_per_stage=2, n_bins=20)
+    st = synth.initial_state(sp, run, lam0=[0.1, 0.3, 0.6, 0.8])
+    e1, _ = make_engine(sp, run, state=st, graph_steps=4)
+    e2, _ = make_engine(sp, run, state=st, graph_steps=4, autotune=1)
+    e1.step(13)
+    e2.step(13)
+    rep = e2.autotune()
+    assert rep.startswith("autotuned")
+    e1.step(11)
+    e2.step(11)
+    for w in range(run.n_walkers):
+        a, b = e1.get_state(w), e2.get_state(w)
+        assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v"], b["v"])
+        assert a["lam"] == b["lam"] and a["plam"] == b["plam"]
+    for stage in range(2):
+        ra, rb = e1.read_abf(0, stage), e2.read_abf(0, stage)
+        assert np.array_equal(ra["sum"], rb["sum"]) and np.array_equal(ra["count"], rb["count"])
+
+
 def test_single_atom_system_and_rebuilds():
     sp = synth.harmonic_well(dims=3)
     run = synth.harmonic_run(n_walkers=4)
