@@ -434,6 +434,28 @@ def harmonic_run(seed: int = 8011, n_walkers: int = 4, n_bins: int = 50, dt: flo
 
 
 # --------------------------------------------------------------------------
+# Fixed-lambda windows (the comparison method of Sec. 4: thermodynamic
+# integration over frozen lambda values)
+# --------------------------------------------------------------------------
+def fixed_lambda_windows(run: RunSpec, windows_per_stage: int, walkers_per_window: int = 1):
+    """The same stages cut into `windows_per_stage` windows each, one bin per
+    window and `walkers_per_window` walkers frozen at each window centre
+    (lambda dynamics and the bias off).  The midpoint-rule sum of the bin
+    means is then the TI estimate over the windows.  Returns (run, lam0)."""
+    stages, lam0 = [], []
+    for st in run.stages:
+        w = (st.hi - st.lo) / windows_per_stage
+        stages.append(Stage(st.lo, st.hi, windows_per_stage, windows_per_stage * walkers_per_window))
+        for k in range(windows_per_stage):
+            lam0 += [st.lo + (k + 0.5) * w] * walkers_per_window
+    out = RunSpec(kT=run.kT, dt=run.dt, gamma=run.gamma, m_lambda=run.m_lambda,
+                  gamma_lambda=run.gamma_lambda, skin=run.skin, n_full=run.n_full,
+                  shared_freq=run.shared_freq, seed=run.seed, stages=stages,
+                  lambda_dynamics=False, abf_on=False, theta_stats=run.theta_stats)
+    return out, lam0
+
+
+# --------------------------------------------------------------------------
 # Initial walker states
 # --------------------------------------------------------------------------
 def initial_state(spec: SystemSpec, run: RunSpec, seed: int | None = None,

@@ -203,6 +203,33 @@ def test_shared_freq_merge_matches_oracle():
 
 
 # ---------------------------------------------------------------------------
+# fixed-lambda windows (Sec. 4 comparison method) and the equal-cost comparison
+# ---------------------------------------------------------------------------
+def test_fixed_lambda_windows_closed_form():
+    sp = synth.harmonic_well(dims=3)
+    run, lam0 = synth.fixed_lambda_windows(synth.harmonic_run(seed=311), 10, 4)
+    st = synth.initial_state(sp, run, lam0=lam0)
+    eng = labf.engine_for(sp, run, st, options=dict(graph_steps=20))
+    eng.step(100_000)
+    assert [eng.get_state(w)["lam"] for w in range(run.n_walkers)] == lam0  # frozen
+    r = eng.read_abf(0, 0)
+    lc = (np.arange(10) + 0.5) / 10
+    np.testing.assert_allclose(r["grad"], 1.5 * 3.0 / (1.0 + 3.0 * lc), rtol=0.08)
+    assert abs(r["dA"] - 1.5 * np.log(4.0)) < 0.05
+
+
+def test_labf_and_windows_at_equal_cost():
+    from paper_2307_08006_gb300 import compare
+    res = compare.compare("harmonic", 200_000, [8100, 8101, 8102], 4)
+    exact = 0.5 * np.log(4.0)
+    assert res["labf"]["walkers"] == res["windows"]["walkers"] == 4
+    assert res["labf"]["steps"] == res["windows"]["steps"]
+    assert abs(res["labf"]["mean"] - exact) < 0.05
+    assert abs(res["windows"]["mean"] - exact) < 0.05
+    assert res["variance_ratio_windows_over_labf"] > 0
+
+
+# ---------------------------------------------------------------------------
 # host-level sharing across engines (Sec. 2.4 walkers on several GPUs)
 # ---------------------------------------------------------------------------
 def _sharing_inputs(seed, shared_freq):

@@ -485,6 +485,26 @@ def test_harmonic_switch_free_energy_closed_form():
 
 
 @pytest.mark.slow
+def test_fixed_lambda_windows_closed_form():
+    """Fixed-lambda windows (the comparison method of Sec. 4): each window's
+    mean <dU/dlambda> is the closed form (d kT/2)(k1 - k0)/k(lambda_c) and the
+    midpoint sum over windows is Delta A = (d kT/2) ln(k1/k0) (the midpoint
+    rule's own error is below 1e-3 here)."""
+    sp = synth.harmonic_well(dims=3)
+    run, lam0 = synth.fixed_lambda_windows(synth.harmonic_run(seed=301), 10, 4)
+    assert not run.lambda_dynamics and run.n_walkers == 40
+    st = synth.initial_state(sp, run, lam0=lam0)
+    sim = oracle.Simulation(sp, run, st)
+    sim.run(100_000)
+    assert np.allclose(sim.a["lam"], lam0)  # frozen
+    grad, A, dA = sim.delta_a(0)
+    lc = (np.arange(10) + 0.5) / 10
+    exact = 1.5 * 3.0 / (1.0 + 3.0 * lc)
+    np.testing.assert_allclose(grad, exact, rtol=0.08)
+    assert dA == pytest.approx(1.5 * np.log(4.0), abs=0.05)
+
+
+@pytest.mark.slow
 def test_harmonic_switch_theta_gradient_closed_form():
     """d Delta A / d k1 = d kT / (2 k1) from the bin estimator with the
     covariance term."""
