@@ -65,6 +65,7 @@ extern "C" {
 
 /* ---- energy terms reported by la_energy_forces ---- */
 #define LA_PAIR_VARIANTS 6
+#define LA_MAX_WALKERS 256 /* walkers per handle, over all its systems */
 #define LA_N_TERMS 7 /* LJ, RF, soft-core LJ, scaled RF, bond, angle, restraint */
 
 /* ---- flags of la_energy_forces ---- */
@@ -95,8 +96,9 @@ typedef struct la_handle la_handle;
  *   lambda_dynamics = 0 freezes lambda (fixed-lambda windows).
  *
  *   ABF (Sec. 2.3, 3.3, 2.4): n_stages stages, each with its own lambda
- *   interval [stage_lo, stage_hi], stage_bins bins and stage_walkers
- *   walkers (walkers are ordered by stage).  The bias is
+ *   interval [stage_lo, stage_hi] inside [0, 1], stage_bins >= 1 bins and
+ *   stage_walkers >= 1 walkers (walkers are ordered by stage; at most
+ *   LA_MAX_WALKERS = 256 walkers over all systems of a handle).  The bias is
  *   min(1, n_k / n_full) * (bin mean); walkers merge their samples into the
  *   shared statistics every shared_freq steps (shared_freq = 0: only when the
  *   host calls la_abf_import).  abf_on = 0 disables the bias.

@@ -84,7 +84,7 @@ int validate(const la_system_desc *sys, int n_sys, std::string &err) {
             return LA_ERR_BOX_TOO_SMALL;
         }
         for (int k = 0; k < S.n_stages; ++k) {
-            if (S.stage_bins[k] <= 0 || S.stage_walkers[k] < 0 || !(S.stage_hi[k] > S.stage_lo[k]) ||
+            if (S.stage_bins[k] <= 0 || S.stage_walkers[k] < 1 || !(S.stage_hi[k] > S.stage_lo[k]) ||
                 S.stage_lo[k] < 0.0 || S.stage_hi[k] > 1.0) {
                 snprintf(buf, sizeof buf, "system %d: invalid stage %d", s, k);
                 err = buf;

@@ -258,6 +258,7 @@ __device__ __forceinline__ void group_sync() {
 template <bool WARP>
 __device__ __forceinline__ void lambda_work(const Dev &d, int si, int prime, int tid, int nt) {
     const StageDev &st = d.stage[si];
+    if (st.w1 <= st.w0) return;  // (create refuses stages without walkers)
     const SysDev &S = d.sys[st.sys];
     if (!prime) {
         // fold each walker's sample into its own statistics (independent)

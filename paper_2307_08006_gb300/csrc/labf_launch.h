@@ -5,7 +5,7 @@
 
 #include "labf_internal.cuh"
 
-#define LA_MAX_WALKERS_PER_LAUNCH 256
+#define LA_MAX_WALKERS_PER_LAUNCH LA_MAX_WALKERS
 
 namespace labf {
 

@@ -38,7 +38,7 @@ def test_library_loads_without_gpu():
 def test_binding_constants_match_header():
     src = open(os.path.join(ROOT, "include", "labf.h")).read()
     defs = {m.group(1): m.group(2) for m in re.finditer(r"^#define (LA_\w+) (\S+)", src, re.M)}
-    for name in ("LA_OK", "LA_WARN_EMPTY_BIN", "LA_N_TERMS", "LA_PAIR_VARIANTS", "LA_N_STATS",
+    for name in ("LA_OK", "LA_WARN_EMPTY_BIN", "LA_N_TERMS", "LA_PAIR_VARIANTS", "LA_MAX_WALKERS", "LA_N_STATS",
                  "LA_N_KERNELS", "LA_EF_REBUILD", "LA_EF_COUNT_PAIRS"):
         assert int(defs[name].rstrip("u"), 0) == getattr(labf, name), name
     for name, v in defs.items():
@@ -93,3 +93,20 @@ def test_query_rejects_bad_input():
     run0 = synth.water_run(walkers_per_stage=1)
     run0.stages = []
     assert _query(sp, run0)[0] == -1
+    # a stage without walkers or bins, an empty lambda interval, a negative
+    # shared_freq
+    for field, value in (("n_walkers", 0), ("n_bins", 0), ("hi", 0.0)):
+        r = synth.water_run(walkers_per_stage=1)
+        setattr(r.stages[1], field, value)
+        assert _query(sp, r)[0] == -1, field
+    r = synth.water_run(walkers_per_stage=1)
+    r.shared_freq = -1
+    assert _query(sp, r)[0] == -1
+
+
+def test_walker_limit():
+    """At most 256 walkers per handle (the pair kernel's per-walker prefix
+    sums live in shared memory)."""
+    sp = synth.lj_fluid()
+    assert _query(sp, synth.lj_fluid_run(n_walkers=256))[0] == 0
+    assert _query(sp, synth.lj_fluid_run(n_walkers=257))[0] == -1

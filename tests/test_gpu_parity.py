@@ -246,6 +246,25 @@ def test_autotune_leaves_the_trajectory_unchanged():
         assert np.array_equal(ra["sum"], rb["sum"]) and np.array_equal(ra["count"], rb["count"])
 
 
+def test_maximum_walkers_and_boundary_lambdas():
+    """256 walkers (the per-handle maximum) in one batched launch, lambda
+    starting exactly on the stage walls, and the empty-bin warning before
+    any sample."""
+    sp = synth.lj_fluid()
+    run = synth.lj_fluid_run(n_walkers=labf.LA_MAX_WALKERS)
+    lam0 = list(np.linspace(0.0, 1.0, run.n_walkers))
+    eng, st = make_engine(sp, run, lam0=lam0)
+    r = eng.read_abf(0, 0)
+    assert r["empty_bin"] and np.isnan(r["grad"]).all() and r["count"].sum() == 0
+    for w in (0, 137, run.n_walkers - 1):
+        check_forces(eng, sp, st, w)
+    eng.step(25)
+    assert eng.sync() == 0
+    assert int(eng.read_abf(0, 0)["count"].sum()) == 25 * run.n_walkers
+    lams = np.array([eng.get_state(w)["lam"] for w in range(run.n_walkers)])
+    assert np.all((lams >= 0.0) & (lams <= 1.0))
+
+
 def test_single_atom_system_and_rebuilds():
     sp = synth.harmonic_well(dims=3)
     run = synth.harmonic_run(n_walkers=4)
