@@ -254,9 +254,12 @@ int la_energy_forces(la_handle *h, int walker, uint32_t flags, double *energy_te
 /*
  * la_get_state / la_set_state: positions, velocities (host [n][3] float32),
  * lambda and p_lambda (host double) and the step counter of one walker, in
- * the system's atom order.  la_set_state rebuilds the lists and re-evaluates
- * forces (no sample is folded).  Any pointer may be NULL (left unchanged /
- * not read).  Synchronising.
+ * the system's atom order.  After la_set_state the walker's lists and
+ * forces (no sample is folded) are rebuilt once, for every walker set since,
+ * before the next call that needs them (la_step_walkers[_plain],
+ * la_energy_forces, la_get_pairs, la_time_kernels, la_autotune,
+ * la_abf_import), so that setting all walkers costs one refresh.  Any
+ * pointer may be NULL (left unchanged / not read).  Synchronising.
  */
 int la_get_state(la_handle *h, int walker, float *x, float *v, double *lam, double *plam,
                  uint64_t *step, void *stream);

@@ -315,6 +315,7 @@ struct la_handle {
     int sticky = LA_OK;
     long long steps = 0, launches = 0, launches_per_step = 0;
     std::string err, report;
+    bool dirty = false;  // a walker's state was set: lists and forces are refreshed lazily
 };
 
 namespace {
@@ -417,6 +418,15 @@ int prime(la_handle *h, int w0, int w1, bool force_rebuild, bool energy, cudaStr
     h->launches += 4 + rebuild_kernel_count(h->hv, w0, w1);
     CU(h, cudaGetLastError());
     return LA_OK;
+}
+
+// lists and forces of walkers whose state la_set_state replaced (their
+// rebuild flags are set), refreshed once for all before the next call
+// that needs forces or lists
+int flush_dirty(la_handle *h, cudaStream_t s) {
+    if (!h->dirty) return LA_OK;
+    h->dirty = false;
+    return prime(h, 0, h->L.W, false, false, s);
 }
 
 int capture_graph(la_handle *h) {
@@ -947,6 +957,8 @@ int la_step_walkers(la_handle *h, int64_t n_steps, void *stream) {
     if (rc != LA_OK) return rc;
     if (n_steps == 0) return LA_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    rc = flush_dirty(h, s);
+    if (rc != LA_OK) return rc;
     const int64_t gs = h->graph_steps;
     const int64_t reps = gs > 0 ? n_steps / gs : 0, rem = gs > 0 ? n_steps % gs : n_steps;
     for (int64_t r = 0; r < reps; ++r) CU(h, cudaGraphLaunch(h->graph, s));
@@ -965,6 +977,8 @@ int la_step_walkers_plain(la_handle *h, int64_t n_steps, void *stream) {
     int rc = check_posted(h);
     if (rc != LA_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    rc = flush_dirty(h, s);
+    if (rc != LA_OK) return rc;
     const int W = h->L.W;
     for (int64_t k = 0; k < n_steps; ++k) {
         // every walker's integrator runs before any rebuild: a walker that
@@ -1038,8 +1052,10 @@ int la_energy_forces(la_handle *h, int walker, uint32_t flags, double *energy_te
     if (walker < 0 || walker >= h->L.W) return fail(h, LA_ERR_INVALID_ARG, "bad walker");
     if (h->sticky != LA_OK) return fail(h, LA_ERR_STATE, "handle in error state: %s", h->err.c_str());
     cudaStream_t s = (cudaStream_t)stream;
+    int rc = flush_dirty(h, s);
+    if (rc != LA_OK) return rc;
     if (flags & LA_EF_COUNT_PAIRS) CU(h, cudaMemsetAsync(h->d.counters + 1, 0, 2 * sizeof(unsigned long long), s));
-    int rc = prime(h, walker, walker + 1, (flags & LA_EF_REBUILD) != 0, true, s);
+    rc = prime(h, walker, walker + 1, (flags & LA_EF_REBUILD) != 0, true, s);
     if (rc != LA_OK) return rc;
     const WalkerDev &W = h->walk[walker];
     const SysDev &S = h->sys[W.sys];
@@ -1095,16 +1111,18 @@ int la_set_state(la_handle *h, int walker, const float *x, const float *v, const
     cudaStream_t s = (cudaStream_t)stream;
     const int n = h->sys[h->walk[walker].sys].n_atoms;
     float *io = (float *)h->io;
-    // read back the current state so that NULL fields stay unchanged
-    launch_state_io(h->d, walker, n, io, io + 3 * (size_t)n, false, s);
-    if (x) CU(h, cudaMemcpyAsync(io, x, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
-    if (v) CU(h, cudaMemcpyAsync(io + 3 * (size_t)n, v, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
-    launch_state_io(h->d, walker, n, io, io + 3 * (size_t)n, true, s);
+    if (x || v) {
+        // read back the current state first when one of the two stays unchanged
+        if (!x || !v) launch_state_io(h->d, walker, n, io, io + 3 * (size_t)n, false, s);
+        if (x) CU(h, cudaMemcpyAsync(io, x, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+        if (v) CU(h, cudaMemcpyAsync(io + 3 * (size_t)n, v, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+        launch_state_io(h->d, walker, n, io, io + 3 * (size_t)n, true, s);
+    }
     if (lam) CU(h, cudaMemcpyAsync(h->d.lam + walker, lam, sizeof(double), cudaMemcpyHostToDevice, s));
     if (plam) CU(h, cudaMemcpyAsync(h->d.plam + walker, plam, sizeof(double), cudaMemcpyHostToDevice, s));
-    CU(h, cudaStreamSynchronize(s));
-    int rc = prime(h, walker, walker + 1, true, false, s);
-    if (rc != LA_OK) return rc;
+    static const int one = 1;
+    CU(h, cudaMemcpyAsync(h->d.rebuild + walker, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+    h->dirty = true;
     return sync_status(h, s, nullptr);
 }
 
@@ -1171,6 +1189,8 @@ int la_abf_import(la_handle *h, int sys, int stage, const double *sum, const dou
     if (sys < 0 || sys >= (int)h->sys.size() || stage < 0 || stage >= h->sys_nstage[sys])
         return fail(h, LA_ERR_INVALID_ARG, "bad system/stage");
     cudaStream_t s = (cudaStream_t)stream;
+    int rc0 = flush_dirty(h, s);
+    if (rc0 != LA_OK) return rc0;
     const StageDev &st = h->stages[h->sys_stage0[sys] + stage];
     const int nb = st.n_bins, MB = h->L.max_bins;
     std::vector<double> s1(nb), s2(nb);
@@ -1261,6 +1281,8 @@ int la_get_pairs(la_handle *h, int walker, int32_t *pairs, uint8_t *kind, int64_
     if (!h || !count) return LA_ERR_INVALID_ARG;
     if (walker < 0 || walker >= h->L.W) return fail(h, LA_ERR_INVALID_ARG, "bad walker");
     cudaStream_t s = (cudaStream_t)stream;
+    int rc0 = flush_dirty(h, s);
+    if (rc0 != LA_OK) return rc0;
     CU(h, cudaStreamSynchronize(s));
     const WalkerDev &W = h->walk[walker];
     const SysDev &S = h->sys[W.sys];
@@ -1380,6 +1402,8 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
     int rc = check_posted(h);
     if (rc != LA_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    rc = flush_dirty(h, s);
+    if (rc != LA_OK) return rc;
     const int W = h->L.W;
     cudaEvent_t ev[LA_N_KERNELS + 1];
     for (auto &e : ev) CU(h, cudaEventCreate(&e));
@@ -1429,6 +1453,8 @@ int la_autotune(la_handle *h, void *stream) {
     int rc = check_posted(h);
     if (rc != LA_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    rc = flush_dirty(h, s);
+    if (rc != LA_OK) return rc;
     rc = sync_status(h, s, nullptr);
     if (rc != LA_OK) return rc;
     rc = tune_pairs(h, s, false);
