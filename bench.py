@@ -168,6 +168,15 @@ def measured_traffic(variant):
     return int(m.group(2)) + int(m.group(3)), "profiles/k_pairs_solvation16.md (ncu, one launch)"
 
 
+def measured_hbm():
+    """HBM copy bandwidth measured on this machine (GB/s), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
 def flush_l2(buf):
     buf.add_(1)  # 256 MB read + write, larger than the 129 MB L2
 
@@ -316,6 +325,12 @@ def gpu_arm(args):
     achieved = pairs_per_md * FLOP_PER_PAIR / (pair_ms * 1e-3) / 1e12
     eng.sync()
     csum = clk.summary(local)
+    # the integrator streams per atom: F (24 B), 1/m and noise scale (8),
+    # v (16), x (16), reference x (16), slot indices (8) read; x, v (32) and
+    # the cleared F (24) written
+    hbm_peak, hbm_src = measured_hbm()
+    integ_bytes = 144.0 * run.n_walkers * spec.n
+    integ_gbs = integ_bytes / (kt["integrate"][0] * 1e-3) / 1e9
 
     m = re.search(r"pair_variant=(\d+)", eng.autotune_report())
     traffic, traffic_src = measured_traffic(int(m.group(1)) if m else -1)
@@ -350,7 +365,13 @@ def gpu_arm(args):
                           kernel="k_pairs (normal + alchemical pairs)",
                           pair_kernel_ms=pair_ms,
                           peak_note=f"{n_sm} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
-                          kernel_ms=dict((k, v[0]) for k, v in kt.items())),
+                          kernel_ms=dict((k, v[0]) for k, v in kt.items()),
+                          timing_note="per-kernel CUDA events on the engine stream over --profile-steps "
+                                      "steps of the one-launch-per-task form, right after the timed region "
+                                      "(kernel nodes of the graph cannot be timed one by one)"),
+            roofline_hbm=dict(bound="hbm", kernel="k_integrate", achieved=integ_gbs, peak=hbm_peak,
+                              unit="GB/s", frac=integ_gbs / hbm_peak, bytes_per_launch=integ_bytes,
+                              peak_source=hbm_src),
             clocks=csum,
             wall_s=wall,
         )

@@ -50,17 +50,21 @@ __global__ void k_integrate(Dev d, int w0, int w1, int g0, int g1) {
         }
     }
     for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += nthr) {
+        // every per-slot load is issued before the first branch (padding
+        // slots are readable too), so they are all in flight together
         const int a = d.atom_of_slot[g];
-        if (a < 0) continue;
         const int w = d.slot_walker[g];
-        const WalkerDev &W = d.walk[w];
-        const SysDev &S = d.sys[W.sys];
         unsigned long long *Fp = d.F + 3 * (size_t)g;
-        float fx = fix_to_float(Fp[0]), fy = fix_to_float(Fp[1]), fz = fix_to_float(Fp[2]);
-        if (fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))) > FIX_LIMIT) set_status(d, LA_STATUS_FIXED_OVERFLOW);
+        const unsigned long long f0 = Fp[0], f1 = Fp[1], f2 = Fp[2];
         const float2 im = d.im[g];
         float4 v = d.vv[g];
         float4 x = d.xq[g];
+        const float4 r = d.xref[g];
+        if (a < 0) continue;
+        const WalkerDev &W = d.walk[w];
+        const SysDev &S = d.sys[W.sys];
+        float fx = fix_to_float(f0), fy = fix_to_float(f1), fz = fix_to_float(f2);
+        if (fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))) > FIX_LIMIT) set_status(d, LA_STATUS_FIXED_OVERFLOW);
         const float hk = 0.5f * S.dt * im.x;
         if (d.pending[w]) {  // final B of the previous step
             v.x += hk * fx;
@@ -96,7 +100,6 @@ __global__ void k_integrate(Dev d, int w0, int w1, int g0, int g1) {
         Fp[1] = 0ull;
         Fp[2] = 0ull;
         // Verlet-buffer criterion: rebuild when an atom moved more than skin/2
-        const float4 r = d.xref[g];
         float dx = min_image(x.x - r.x, S.boxf, S.box_invf);
         float dy = min_image(x.y - r.y, S.boxf, S.box_invf);
         float dz = min_image(x.z - r.z, S.boxf, S.box_invf);
