@@ -146,7 +146,8 @@ class ClockSampler:
 
 def measured_traffic(variant):
     """DRAM bytes per pair-kernel launch from the committed ncu summary, or
-    None when that capture is of another variant or of older kernel source."""
+    None when the capture is of older kernel source.  The fused step launch
+    is preferred; otherwise the one-task launch of the same variant."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "k_pairs_solvation16.md")
@@ -154,18 +155,20 @@ def measured_traffic(variant):
         text = open(path).read()
     except OSError:
         return None, "no capture"
-    m = re.search(r"traffic_bytes_per_launch: variant=(\d+) dram_read=(\d+) dram_write=(\d+) "
-                  r"source_sha256=(\w+)", text)
-    if not m:
+    lines = re.findall(r"traffic_bytes_per_launch: variant=(\d+) form=(\w+) dram_bytes=(\d+) "
+                       r"source_sha256=(\w+)", text)
+    if not lines:
         return None, "no capture"
     h = hashlib.sha256()
-    for f in ("k_pairs.cu", "labf_internal.cuh"):
+    for f in ("k_pairs.cu", "labf_internal.cuh", "labf_dyn.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2307_08006_gb300", "csrc", f), "rb").read())
-    if h.hexdigest()[:16] != m.group(4):
+    if h.hexdigest()[:16] != lines[0][3]:
         return None, "kernel source changed since the capture"
-    if int(m.group(1)) != variant:
-        return None, f"capture is of pair_variant={m.group(1)}"
-    return int(m.group(2)) + int(m.group(3)), "profiles/k_pairs_solvation16.md (ncu, one launch)"
+    for form in ("fused", "single"):
+        for v, fm, b, _ in lines:
+            if int(v) == variant and fm == form:
+                return int(b), f"profiles/k_pairs_solvation16.md (ncu, {form} launch, variant {v})"
+    return None, f"no capture of pair_variant={variant}"
 
 
 def measured_hbm():
