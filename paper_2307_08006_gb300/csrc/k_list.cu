@@ -387,11 +387,13 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
         // (padding or alchemical)
         for (int k = lane; k < SC; k += 32) {
             int4 u = d.uq[gS + k];
-            const int2 m = d.smeta[gS + k];
+            int2 m = d.smeta[gS + k];
+            const int4 e = d.sexcl[gS + k];
             if (m.y) u.w = -1;
+            m.y = (e.x & e.y & e.z & e.w) != -1;  // staged .y: the slot has extra exclusions
             s_u[wib][k] = u;
             s_m[wib][k] = m;
-            s_e[wib][k] = d.sexcl[gS + k];
+            s_e[wib][k] = e;
         }
         if (lane < 2 * NIC) s_bb[wib][lane] = d.bb_ic[2 * (size_t)s * NIC + lane];
         __syncwarp();
@@ -423,11 +425,13 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
             __syncwarp();
             for (int k = lane; k < SC; k += 32) {
                 int4 u = d.uq[gT + k];
-                const int2 m = d.smeta[gT + k];
+                int2 m = d.smeta[gT + k];
+                const int4 e = d.sexcl[gT + k];
                 if (m.y) u.w = -1;
+                m.y = (e.x & e.y & e.z & e.w) != -1;
                 t_u[wib][k] = u;
                 t_m[wib][k] = m;
-                t_e[wib][k] = d.sexcl[gT + k];
+                t_e[wib][k] = e;
             }
             t_bb[wib][lane] = d.bb_jc[2 * (size_t)t * NJC + lane];
             __syncwarp();
@@ -464,27 +468,25 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
                     const int4 uj = t_u[wib][jc * JC + jb];
                     const int2 mj = t_m[wib][jc * JC + jb];
                     const int4 ej = t_e[wib][jc * JC + jb];
-                    unsigned lbyte = 0, imask = 0;
+                    const int ujx = uj.x + shx, ujy = uj.y + shy, ujz = uj.z + shz;
+                    const int jlim = self0 ? jc * JC + jb : SC;  // same cluster set: slot_i < slot_j
+                    unsigned lbyte = 0;
                     for (unsigned m = cand; m; m &= m - 1u) {  // candidate i-clusters, ascending
                         const int ic = __ffs(m) - 1;
                         const int si = ic * IC + ia;
                         const int4 ui = s_u[wib][si];
-                        bool ok = (ui.w | uj.w) >= 0;
-                        if (self0) ok = ok && si < jc * JC + jb;
+                        const int2 mi = s_m[wib][si];
                         // D < R implies every component lies in (-2^23, 2^23) (R <= 2^46
                         // because L >= 2 r_list), i.e. this shift is the minimum image
-                        const int dx = uj.x + shx - ui.x, dy = uj.y + shy - ui.y, dz = uj.z + shz - ui.z;
-                        ok = ok && (long long)dx * dx + (long long)dy * dy + (long long)dz * dz < R;
-                        if (ok) {
-                            const int4 ei = s_e[wib][si];
-                            const int2 mi = s_m[wib][si];
-                            if (mi.x >= 0 && mi.x == mj.x) ok = false;
-                            else if ((ei.x & ei.y & ei.z & ei.w & ej.x & ej.y & ej.z & ej.w) != -1)
-                                ok = !excluded_meta(ui.w, mi, ei, uj.w, mj, ej);  // some partner list is not empty
-                        }
-                        if (ok) lbyte |= 1u << ic;
-                        if (__any_sync(0xffffffffu, ok)) imask |= 1u << ic;
+                        const int dx = ujx - ui.x, dy = ujy - ui.y, dz = ujz - ui.z;
+                        bool ok = (ui.w | uj.w) >= 0 && si < jlim &&
+                                  (long long)dx * dx + (long long)dy * dy + (long long)dz * dz < R &&
+                                  !(mi.x >= 0 && mi.x == mj.x);
+                        if (ok && (mi.y | mj.y))  // extra partner lists
+                            ok = !excluded_meta(ui.w, mi, s_e[wib][si], uj.w, mj, ej);
+                        lbyte |= (unsigned)ok << ic;
                     }
+                    const unsigned imask = __reduce_or_sync(0xffffffffu, lbyte);
                     if (imask) {
                         if (nent < d.sub_cap) {
                             const size_t e = ebase + nent;
