@@ -22,8 +22,9 @@ namespace labf {
 // ---------------------------------------------------------------------------
 __global__ void k_integrate(Dev d, int w0, int w1, int g0, int g1) {
     const int nthr = gridDim.x * blockDim.x;
-    // lambda particles: handled by the first w1-w0 threads of the last block
-    if (blockIdx.x == gridDim.x - 1) {
+    // lambda particles (FP64): the first w1-w0 threads of block 0, which is
+    // scheduled first, so that this work overlaps the atoms'
+    if (blockIdx.x == 0) {
         int w = w0 + threadIdx.x;
         if (w < w1) {
             const SysDev &S = d.sys[d.walk[w].sys];
