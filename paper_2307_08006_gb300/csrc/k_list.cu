@@ -162,23 +162,42 @@ __global__ void __launch_bounds__(128) k_kdsplit(Dev d, int w0, int w1) {
         __syncwarp();
         // leaf index by four binary splits
         for (int level = 0; level < 4; ++level) {
+            // extent and size of every group of this level by warp reductions;
+            // each lane keeps those of its two atoms' groups
+            int ext[2][3] = {{0, 0, 0}, {0, 0, 0}}, cnts[2] = {0, 0};
+            {
+                const int ga = lane < n ? sg[wib][lane] : -1;
+                const int gb = lane + 32 < n ? sg[wib][lane + 32] : -1;
+                const int xa[3] = {sx[wib][lane], sy[wib][lane], sz[wib][lane]};
+                const int xb[3] = {sx[wib][lane + 32], sy[wib][lane + 32], sz[wib][lane + 32]};
+                for (int g = 0; g < (1 << level); ++g) {
+                    const bool ia = ga == g, ib = gb == g;
+                    const int c = __reduce_add_sync(0xffffffffu, (int)ia + (int)ib);
+                    for (int q = 0; q < 3; ++q) {
+                        const int lo = __reduce_min_sync(0xffffffffu, min(ia ? xa[q] : (1 << 30), ib ? xb[q] : (1 << 30)));
+                        const int hi = __reduce_max_sync(0xffffffffu, max(ia ? xa[q] : -1, ib ? xb[q] : -1));
+                        if (ia) ext[0][q] = hi - lo;
+                        if (ib) ext[1][q] = hi - lo;
+                    }
+                    if (ia) cnts[0] = c;
+                    if (ib) cnts[1] = c;
+                }
+            }
             int newg[2];
+#pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int k = lane + 32 * h;
                 newg[h] = sg[wib][k];
                 if (k >= n) continue;
                 const int gid = sg[wib][k];
-                int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-1, -1, -1}, cnt = 0;
-                for (int m = 0; m < n; ++m) {
-                    if (sg[wib][m] != gid) continue;
-                    ++cnt;
-                    mn[0] = min(mn[0], sx[wib][m]); mx[0] = max(mx[0], sx[wib][m]);
-                    mn[1] = min(mn[1], sy[wib][m]); mx[1] = max(mx[1], sy[wib][m]);
-                    mn[2] = min(mn[2], sz[wib][m]); mx[2] = max(mx[2], sz[wib][m]);
+                const int cnt = cnts[h];
+                // longest axis, the first of equal ones
+                int ax = 0, eb = ext[h][0];
+                if (ext[h][1] > eb) {
+                    ax = 1;
+                    eb = ext[h][1];
                 }
-                int ax = 0;
-                if (mx[1] - mn[1] > mx[ax] - mn[ax]) ax = 1;
-                if (mx[2] - mn[2] > mx[ax] - mn[ax]) ax = 2;
+                if (ext[h][2] > eb) ax = 2;
                 const int *co = ax == 0 ? sx[wib] : (ax == 1 ? sy[wib] : sz[wib]);
                 const long long mykey = ((long long)co[k] << 32) | (unsigned)sa[wib][k];
                 int r = 0;
