@@ -55,7 +55,7 @@ def walker_ns_per_day(n_walkers, md_steps, dt_ps, seconds):
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(steps=2):
+def cpu_baseline(steps=2, single_thread=False):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of
     the same workload (all 16 walkers, `steps` MD steps, OpenMP over walkers)."""
     import oracle
@@ -71,9 +71,23 @@ def cpu_baseline(steps=2):
     sim.run(steps)
     dt = time.perf_counter() - t0
     val = walker_ns_per_day(run.n_walkers, steps, run.dt, dt)
-    return dict(value=val, unit=UNIT, cores=cores, kind="oracle",
-                sample=f"{run.n_walkers} walkers x {steps} MD steps of the same workload "
-                       f"(O(N^2) FP64, OpenMP over walkers), {dt:.2f} s"), dt
+    out = dict(value=val, unit=UNIT, cores=cores, kind="oracle",
+               sample=f"{run.n_walkers} walkers x {steps} MD steps of the same workload "
+                      f"(O(N^2) FP64, OpenMP over walkers), {dt:.2f} s")
+    if single_thread:
+        # the same oracle on one core: one walker of each stage, one MD step
+        from dataclasses import replace
+
+        run1 = replace(run, stages=[replace(s_, n_walkers=1) for s_ in run.stages])
+        oracle.set_threads(1)
+        sim1 = oracle.Simulation(spec, run1, synth.initial_state(spec, run1))
+        t1 = time.perf_counter()
+        sim1.run(1)
+        d1 = time.perf_counter() - t1
+        oracle.set_threads(cores)
+        out["single_thread"] = dict(value=walker_ns_per_day(run1.n_walkers, 1, run.dt, d1), unit=UNIT, cores=1,
+                                    sample=f"{run1.n_walkers} walkers x 1 MD step, one thread, {d1:.2f} s")
+    return out, dt
 
 
 def reference_arm(args):
@@ -340,7 +354,7 @@ def gpu_arm(args):
     if rank == 0:
         cb = None
         if world == 1 and not args.no_cpu_baseline:
-            cb, _ = cpu_baseline(steps=args.cpu_steps)
+            cb, _ = cpu_baseline(steps=args.cpu_steps, single_thread=True)
         line = dict(
             metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
             ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,

@@ -123,6 +123,33 @@ def test_autograd_gradients_match_oracle_at_21_lambdas():
 
 
 # ---------------------------------------------------------------------------
+# the benchmark's own workload and launch configuration, full size
+# ---------------------------------------------------------------------------
+def test_bench_workload_full_size():
+    """16 walkers x 12 300 atoms with the bench's options (autotuned pair
+    kernel, 20-step CUDA graph with the fused pair launch): 20 graph steps
+    are bit-identical to 20 steps of the one-walker-per-launch form, and
+    sampled forces and dU/dlambda of three walkers match the oracle."""
+    import bench
+
+    spec, run = bench.workload()
+    state = synth.initial_state(spec, run)
+    e1 = labf.Engine([labf.SystemInput(spec, run, state)], options=dict(graph_steps=20, autotune=1))
+    e2 = labf.Engine([labf.SystemInput(spec, run, state)], options=dict(graph_steps=20))
+    e1.step(20)
+    e2.step_plain(20)
+    assert e1.sync() == 0 and e2.sync() == 0
+    for w in range(run.n_walkers):
+        a, b = e1.get_state(w), e2.get_state(w)
+        assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["v"], b["v"])
+        assert a["lam"] == b["lam"] and a["plam"] == b["plam"]
+    atoms = sample_atoms(spec, 48, 13, extra=np.nonzero(spec.alch)[0])
+    for w in (0, 9, 15):
+        s = e1.get_state(w)
+        check_sampled(e1, w, spec, s["x"], s["lam"], atoms)
+
+
+# ---------------------------------------------------------------------------
 # large restrained complex: 96k atoms, sampled forces (incl. restraints)
 # ---------------------------------------------------------------------------
 def test_large_complex_sampled_forces_and_steps():
