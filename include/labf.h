@@ -153,6 +153,11 @@ typedef struct {
     int32_t pair_ctas_per_sm;    /* pair grid in 8-warp CTA equivalents per SM (0 = 4) */
     int32_t chunk_entries;       /* cluster-pair entries per warp work item, a multiple of
                                     32 (0 = 32) */
+    double prune_margin;         /* dynamic pruning of the batched step: tiles with no
+                                    listed pair within r_cut + prune_margin are skipped
+                                    until some atom moves 0.45 prune_margin (then they
+                                    are re-pruned); 0 = skin / 3, < 0 or >= skin = off.
+                                    Results are identical either way. */
 } la_options;
 
 /*
@@ -321,21 +326,24 @@ int la_sync(la_handle *h, void *stream, uint32_t *status_bits);
  *   [3] in-cutoff normal pairs counted by the last LA_EF_COUNT_PAIRS call,
  *   [4] in-cutoff alchemical pairs counted by that call,
  *   [5] cluster-pair entries in the current lists (all walkers),
- *   [6] 8 x 4 atom-pair tiles in the current lists (all walkers); each tile
- *       is one warp-wide evaluation of 32 candidate pairs.
+ *   [6] 8 x 4 atom-pair tiles the batched step evaluates (all walkers, after
+ *       the last dynamic pruning); each tile is one warp-wide evaluation of
+ *       32 candidate pairs.
  * Synchronising.
  */
 #define LA_N_STATS 7
 int la_stats(la_handle *h, int64_t *out, void *stream);
 
 /*
- * la_time_kernels: run n_steps batched steps outside the graph with CUDA
- * events around each kernel on `stream`; ms_out (host [LA_N_KERNELS])
- * receives the mean device milliseconds per launch of each kernel class,
- * launches_out (host [LA_N_KERNELS], may be NULL) the launch counts.
- * Synchronising.
+ * la_time_kernels: run n_steps batched steps outside the graph, the same
+ * launches as the graph's, with CUDA events between them on `stream`;
+ * ms_out (host [LA_N_KERNELS]) receives the mean device milliseconds per
+ * step of each kernel class, launches_out (host [LA_N_KERNELS], may be NULL)
+ * the launch counts.  In the batched step the bonded terms, the walker terms
+ * and the lambda update run inside the pair launch, so their classes read 0
+ * and "pairs" is the whole fused launch.  Synchronising.
  */
-#define LA_N_KERNELS 6 /* integrate, rebuild (all list kernels), pairs, bonded, walker, lambda */
+#define LA_N_KERNELS 6 /* integrate, rebuild (list kernels + pruning), pairs, bonded, walker, lambda */
 int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_out, void *stream);
 
 /*

@@ -100,7 +100,9 @@ __device__ __forceinline__ void flush_j(const Dev &d, int gj, int ia, float fjx,
         atomicAdd(d.F + 3 * (size_t)gj + (ia >> 1), (unsigned long long)__float2ll_rn(-c * F_TO_FIX));
 }
 
-template <bool ENERGY, int WARPS>
+// MSHIFT: 8 reads the i-cluster mask pruned for the batched step, 16 the
+// listed one (one-task launches, which run without pruning)
+template <bool ENERGY, int WARPS, int MSHIFT>
 __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int nblk, PairShared<WARPS> &sh) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int ia = lane & 7, jb = lane >> 3;
@@ -144,7 +146,7 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
             if (lane < ne) {
                 const int2 hdr = d.ent_hdr[ebase + eb + lane];
                 gj_l = hdr.x;
-                im_l = ((unsigned)hdr.y >> 8) & 0xffu;
+                im_l = ((unsigned)hdr.y >> MSHIFT) & 0xffu;
                 const float sx = (float)((hdr.y & 3) - 1) * L;
                 const float sy = (float)(((hdr.y >> 2) & 3) - 1) * L;
                 const float sz = (float)(((hdr.y >> 4) & 3) - 1) * L;
@@ -165,6 +167,7 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
             __syncwarp();
             for (int k = 0; k < ne; ++k) {
                 const unsigned imask = __shfl_sync(FULL, im_l, k);
+                if (!imask) continue;  // every tile pruned: nothing to add
                 const int gj = __shfl_sync(FULL, gj_l, k) + jb;
                 const float4 xj = sh.jx[wib][k][jb];
                 const float2 lj_j = sh.jl[wib][k][jb];
@@ -284,7 +287,7 @@ struct PairShared2 {
     int pre[LA_MAX_WALKERS_PER_LAUNCH + 1];
 };
 
-template <int WARPS>
+template <int WARPS, int MSHIFT>
 __device__ __forceinline__ void normal_items_x2(const Dev &d, int w0, int w1, int nblk, PairShared2<WARPS> &sh) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int ia = lane & 7, jb = lane >> 3;
@@ -336,7 +339,7 @@ __device__ __forceinline__ void normal_items_x2(const Dev &d, int w0, int w1, in
             if (lane < ne) {
                 const int2 hdr = d.ent_hdr[ebase + eb + lane];
                 gj_l = hdr.x;
-                im_l = ((unsigned)hdr.y >> 8) & 0xffu;
+                im_l = ((unsigned)hdr.y >> MSHIFT) & 0xffu;
                 const float sx = (float)((hdr.y & 3) - 1) * L;
                 const float sy = (float)(((hdr.y >> 2) & 3) - 1) * L;
                 const float sz = (float)(((hdr.y >> 4) & 3) - 1) * L;
@@ -359,6 +362,7 @@ __device__ __forceinline__ void normal_items_x2(const Dev &d, int w0, int w1, in
             __syncwarp();
             for (int k = 0; k < ne; ++k) {
                 const unsigned imask = __shfl_sync(FULL, im_l, k);
+                if (!imask) continue;  // every tile pruned: nothing to add
                 const int gj = __shfl_sync(FULL, gj_l, k) + jb;
                 const unsigned lb = sh.lb[wib][k][lane];
                 touched |= imask;
@@ -623,7 +627,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(Dev d, int w0, int w
         sh.pre[w1 - w0] = acc;
     }
     __syncthreads();
-    normal_items<ENERGY, WARPS>(d, w0, w1, nblk_pairs, sh);
+    normal_items<ENERGY, WARPS, FUSED ? 8 : 16>(d, w0, w1, nblk_pairs, sh);
 }
 
 template <int WARPS, int MINB, bool FUSED>
@@ -648,7 +652,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_x2(Dev d, int w0, in
         sh.pre[w1 - w0] = acc;
     }
     __syncthreads();
-    normal_items_x2<WARPS>(d, w0, w1, nblk_pairs, sh);
+    normal_items_x2<WARPS, FUSED ? 8 : 16>(d, w0, w1, nblk_pairs, sh);
 }
 
 template <bool ENERGY, int WARPS, int MINB, bool X2 = false>

@@ -222,6 +222,7 @@ size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io
     d.xq = a.take<float4>(L.slots);
     d.vv = a.take<float4>(L.slots);
     d.xref = a.take<float4>(L.slots);
+    d.xprune = a.take<float4>(L.slots);
     d.lj = a.take<float2>(L.slots);
     d.im = a.take<float2>(L.slots);
     d.atom_of_slot = a.take<int>(L.slots);
@@ -269,6 +270,7 @@ size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io
     d.step = a.take<unsigned long long>(L.W);
     d.pending = a.take<int>(L.W);
     d.rebuild = a.take<int>(L.W);
+    d.prune = a.take<int>(L.W);
     d.eterm = a.take<long long>((size_t)L.W * N_ETERMS);
     d.abf_sum = a.take<double>(L.total_bins);
     d.abf_sumsq = a.take<double>(L.total_bins);
@@ -392,11 +394,12 @@ int sync_status(la_handle *h, cudaStream_t s, unsigned *bits) {
 int enqueue_step(la_handle *h, int w0, int w1, cudaStream_t s) {
     launch_integrate(h->d, h->hv, w0, w1, s);
     launch_rebuild(h->d, h->hv, w0, w1, s);
+    launch_prune(h->d, h->hv, w0, w1, s);
     launch_pairs_fused(h->d, h->hv, (int)h->stages.size(), s);
     return 0;
 }
 
-int kernels_per_step(la_handle *h) { return 1 + rebuild_kernel_count(h->hv, 0, h->L.W) + 1; }
+int kernels_per_step(la_handle *h) { return 1 + rebuild_kernel_count(h->hv, 0, h->L.W) + 1 + 1; }
 
 // evaluate forces, dU/dlambda and G at the current state of walkers [w0, w1)
 int prime(la_handle *h, int w0, int w1, bool force_rebuild, bool energy, cudaStream_t s) {
@@ -451,31 +454,40 @@ int capture_graph(la_handle *h) {
         const cudaGraphNode_t *deps = nullptr;
         size_t nd = 0;
         CU(h, cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, nullptr, nullptr, nullptr));
-        cudaGraphConditionalHandle hc;
+        cudaGraphConditionalHandle hc, hp;
         CU(h, cudaGraphConditionalHandleCreate(&hc, cg, 0, cudaGraphCondAssignDefault));
-        launch_gate(h->d, 0, W, hc, cs);
+        CU(h, cudaGraphConditionalHandleCreate(&hp, cg, 0, cudaGraphCondAssignDefault));
+        launch_gate(h->d, 0, W, hc, hp, cs);
         CU(h, cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, &deps, nullptr, &nd));
-        cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
-        p.conditional.handle = hc;
-        p.conditional.type = cudaGraphCondTypeIf;
-        p.conditional.size = 1;
-        cudaGraphNode_t cn;
-        CU(h, cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &p));
-        cudaGraph_t body = p.conditional.phGraph_out[0];
-        CU(h, cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        launch_rebuild(h->d, h->hv, 0, W, cb);
-        cudaGraph_t body_out;
-        CU(h, cudaStreamEndCapture(cb, &body_out));
-        CU(h, cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+        // IF (some walker must rebuild) { list kernels }, then
+        // IF (some walker must prune, or rebuilt) { prune }
+        cudaGraphNode_t prev = nullptr;
+        for (int q = 0; q < 2; ++q) {
+            cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+            p.conditional.handle = q == 0 ? hc : hp;
+            p.conditional.type = cudaGraphCondTypeIf;
+            p.conditional.size = 1;
+            cudaGraphNode_t cn;
+            if (q == 0) CU(h, cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &p));
+            else CU(h, cudaGraphAddNode(&cn, cg, &prev, nullptr, 1, &p));
+            cudaGraph_t body = p.conditional.phGraph_out[0];
+            CU(h, cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            if (q == 0) launch_rebuild(h->d, h->hv, 0, W, cb);
+            else launch_prune(h->d, h->hv, 0, W, cb);
+            cudaGraph_t body_out;
+            CU(h, cudaStreamEndCapture(cb, &body_out));
+            prev = cn;
+        }
+        CU(h, cudaStreamUpdateCaptureDependencies(cs, &prev, nullptr, 1, cudaStreamSetCaptureDependencies));
         launch_pairs_fused(h->d, h->hv, (int)h->stages.size(), cs);
     }
     CU(h, cudaStreamEndCapture(cs, &g));
     cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, LA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    // graph steps: integrate, gate, fused pairs; list kernels are counted per
-    // executed rebuild (device counter)
-    h->graph_launches_per_step = h->launches_per_step - rebuild_kernel_count(h->hv, 0, W) + 1;
+    // graph steps: integrate, gate, fused pairs; list and prune kernels are
+    // counted per executed rebuild and pruning (device counters)
+    h->graph_launches_per_step = h->launches_per_step - rebuild_kernel_count(h->hv, 0, W) - 1 + 1;
     return LA_OK;
 }
 
@@ -718,6 +730,15 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         D.sd_lm = std::sqrt(std::max(0.0, (1.0 - D.c_lm * D.c_lm) * S.m_lambda * S.kT));
         D.kT = S.kT;
         D.half_skin2 = (float)(0.25 * S.skin * S.skin);
+        {
+            const double pm = h->opt.prune_margin == 0.0 ? S.skin / 3.0 : h->opt.prune_margin;
+            const bool on = pm > 0.0 && pm < S.skin;
+            // a pruned tile holds no listed pair within r_c + pm; pruning is redone
+            // once an atom moved 0.45 pm, so every pair moves less than 0.9 pm in
+            // between (the 0.1 pm left covers FP32 rounding near the cutoff)
+            D.prune_disp2 = on ? (float)(0.2025 * pm * pm) : 0.f;
+            D.rprune2 = on ? (float)((S.r_cut + pm) * (S.r_cut + pm)) : 0.f;
+        }
         const double binv = 1.0 / S.box;
         const double a_ = sl.r_list * binv;
         D.R = (long long)std::floor((a_ * a_) * 281474976710656.0);
@@ -1303,7 +1324,7 @@ int la_get_pairs(la_handle *h, int walker, int32_t *pairs, uint8_t *kind, int64_
         for (int e = 0; e < nent[W.sc_off + sl - W.sc_off]; ++e) {
             const size_t ge = (size_t)sl * h->L.ent_cap + e;
             const int jbase = hdr[ge].x - W.slot_off;
-            const unsigned imask = ((unsigned)hdr[ge].y >> 8) & 0xffu;
+            const unsigned imask = ((unsigned)hdr[ge].y >> 16) & 0xffu;  // listed, not pruned
             for (int ic = 0; ic < NIC; ++ic) {
                 if (!(imask & (1u << ic))) continue;
                 for (int lane = 0; lane < 32; ++lane) {
@@ -1388,7 +1409,7 @@ int la_stats(la_handle *h, int64_t *out, void *stream) {
         out[0] = h->steps;
         out[1] = (int64_t)c[0];
         // list kernels run inside the graph only on rebuild steps (counted by the gate)
-        out[2] = h->launches + (int64_t)c[6] * rebuild_kernel_count(h->hv, 0, h->L.W);
+        out[2] = h->launches + (int64_t)c[6] * rebuild_kernel_count(h->hv, 0, h->L.W) + (int64_t)c[7];
         out[3] = (int64_t)c[1];
         out[4] = (int64_t)c[2];
         out[5] = ents;
@@ -1409,20 +1430,19 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
     for (auto &e : ev) CU(h, cudaEventCreate(&e));
     double acc[LA_N_KERNELS] = {0};
     int64_t cnt[LA_N_KERNELS] = {0};
-    const int nbo = h->hv.bo_off[W - 1] + h->hv.n_bo[W - 1];
     for (int k = 0; k < n_steps; ++k) {
         cudaEventRecord(ev[0], s);
         launch_integrate(h->d, h->hv, 0, W, s);
         cudaEventRecord(ev[1], s);
         launch_rebuild(h->d, h->hv, 0, W, s);
+        launch_prune(h->d, h->hv, 0, W, s);
         cudaEventRecord(ev[2], s);
-        launch_pairs(h->d, h->hv, 0, W, false, s);
+        // the fused launch of the batched step: pairs, bonded terms, walker
+        // terms and the lambda update
+        launch_pairs_fused(h->d, h->hv, (int)h->stages.size(), s);
         cudaEventRecord(ev[3], s);
-        launch_bonded(h->d, h->hv, 0, W, false, s);
         cudaEventRecord(ev[4], s);
-        launch_walker(h->d, 0, W, false, s);
         cudaEventRecord(ev[5], s);
-        launch_lambda(h->d, 0, (int)h->stages.size(), false, s);
         cudaEventRecord(ev[6], s);
         CU(h, cudaEventSynchronize(ev[6]));
         for (int q = 0; q < LA_N_KERNELS; ++q) {
@@ -1431,11 +1451,8 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
             acc[q] += ms;
         }
         cnt[0] += 1;
-        cnt[1] += rebuild_kernel_count(h->hv, 0, W);
+        cnt[1] += rebuild_kernel_count(h->hv, 0, W) + 1;
         cnt[2] += 1;
-        cnt[3] += nbo > 0 ? 1 : 0;
-        cnt[4] += 1;
-        cnt[5] += 1;
     }
     launch_finish(h->d, h->hv, 0, W, s);
     h->steps += n_steps;

@@ -51,6 +51,8 @@ struct SysDev {
     float dt, c_at, s_at;         // atoms: dt, exp(-gamma dt), sqrt(1 - c^2)
     double dt_d, m_lambda, c_lm, sd_lm, kT;  // lambda particle
     float half_skin2;             // (skin / 2)^2
+    float prune_disp2;            // squared displacement that triggers pruning (0: off)
+    float rprune2;                // (r_c + prune margin)^2
     long long R;                  // integer list threshold
     int Rq;                       // list radius in quantized units (rounded up)
     int ncx;                      // columns per dimension
@@ -162,6 +164,8 @@ struct Dev {
     // status and counters
     unsigned int *status;
     unsigned int *wdone, *sdone;  // arrivals per walker / per stage in the fused pair launch
+    float4 *xprune;               // positions at the last pruning, per slot
+    int *prune;                   // per walker: prune the tiles before the next fused step
     unsigned long long *counters; // [0] rebuilds [1] pairs normal [2] pairs alch [4, 5] pair
                                   // work items [6] rebuild events [8, 9] list-build work items
 };

@@ -76,7 +76,8 @@ class la_system_desc(C.Structure):
 class la_options(C.Structure):
     _fields_ = [("graph_steps", C.c_int32), ("autotune", C.c_int32),
                 ("list_capacity_factor", C.c_double), ("pair_variant", C.c_int32),
-                ("pair_ctas_per_sm", C.c_int32), ("chunk_entries", C.c_int32)]
+                ("pair_ctas_per_sm", C.c_int32), ("chunk_entries", C.c_int32),
+                ("prune_margin", C.c_double)]
 
 
 _lib = None
