@@ -156,7 +156,7 @@ typedef struct {
     double prune_margin;         /* dynamic pruning of the batched step: tiles with no
                                     listed pair within r_cut + prune_margin are skipped
                                     until some atom moves 0.45 prune_margin (then they
-                                    are re-pruned); 0 = skin / 3, < 0 or >= skin = off.
+                                    are re-pruned); 0 (default), < 0 or >= skin = off.
                                     Results are identical either way. */
 } la_options;
 

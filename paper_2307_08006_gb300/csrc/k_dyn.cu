@@ -61,7 +61,6 @@ __global__ void k_integrate(Dev d, int w0, int w1, int g0, int g1) {
         float4 v = d.vv[g];
         float4 x = d.xq[g];
         const float4 r = d.xref[g];
-        const float4 rp = d.xprune[g];
         if (a < 0) continue;
         const WalkerDev &W = d.walk[w];
         const SysDev &S = d.sys[W.sys];
@@ -111,6 +110,7 @@ __global__ void k_integrate(Dev d, int w0, int w1, int g0, int g1) {
             for (int k = 0; k < S.w_count; ++k) d.rebuild[S.w_first + k] = 1;
         // the same for the pruned tiles of the batched step
         if (S.prune_disp2 > 0.f) {
+            const float4 rp = d.xprune[g];
             dx = min_image(x.x - rp.x, S.boxf, S.box_invf);
             dy = min_image(x.y - rp.y, S.boxf, S.box_invf);
             dz = min_image(x.z - rp.z, S.boxf, S.box_invf);

@@ -724,37 +724,34 @@ __global__ void k_items(Dev d, int w0) {
         if (carry > W.item_cap) set_status(d, LA_STATUS_LIST_OVERFLOW);
         d.n_items[w] = min(carry, W.item_cap);
         d.rebuild[w] = 0;
-        d.prune[w] = 1;  // fresh lists: prune before the next batched pair pass
+        if (d.sys[W.sys].prune_disp2 > 0.f) d.prune[w] = 1;  // fresh lists: prune before the next batched pass
         atomicAdd(&d.counters[0], 1ull);
     }
 }
 
 // -------------------------------------------------------------------------
 // gate of the rebuild chain inside a CUDA graph: one thread sets the step's
-// conditional handle to "some walker must rebuild", so that the graph skips
-// the whole chain otherwise; rebuild events are counted in counters[6]
+// conditional handle to "some walker must rebuild or prune", so that the
+// graph skips the whole chain otherwise; such steps are counted in
+// counters[6]
 // -------------------------------------------------------------------------
-__global__ void k_gate(Dev d, int w0, int w1, cudaGraphConditionalHandle handle,
-                       cudaGraphConditionalHandle handle_prune) {
-    __shared__ int any, anyp;
-    if (threadIdx.x == 0) any = anyp = 0;
+__global__ void k_gate(Dev d, int w0, int w1, cudaGraphConditionalHandle handle) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
     __syncthreads();
-    for (int w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
-        if (d.rebuild[w]) any = 1;
-        if (d.prune[w]) anyp = 1;
-    }
+    for (int w = w0 + threadIdx.x; w < w1; w += blockDim.x)
+        if (d.rebuild[w] | d.prune[w]) any = 1;
     __syncthreads();
     if (threadIdx.x == 0) {
+        // the body (list kernels, then pruning) runs when some walker must
+        // rebuild or prune; every kernel in it skips walkers not flagged
         cudaGraphSetConditional(handle, any ? 1u : 0u);
-        cudaGraphSetConditional(handle_prune, (any | anyp) ? 1u : 0u);  // a rebuild is pruned too
         if (any) atomicAdd(&d.counters[6], 1ull);
-        if (any | anyp) atomicAdd(&d.counters[7], 1ull);
     }
 }
 
-void launch_gate(const Dev &d, int w0, int w1, cudaGraphConditionalHandle handle,
-                 cudaGraphConditionalHandle handle_prune, cudaStream_t s) {
-    k_gate<<<1, 256, 0, s>>>(d, w0, w1, handle, handle_prune);
+void launch_gate(const Dev &d, int w0, int w1, cudaGraphConditionalHandle handle, cudaStream_t s) {
+    k_gate<<<1, 256, 0, s>>>(d, w0, w1, handle);
 }
 
 // -------------------------------------------------------------------------

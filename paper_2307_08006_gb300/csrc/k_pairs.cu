@@ -167,7 +167,6 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
             __syncwarp();
             for (int k = 0; k < ne; ++k) {
                 const unsigned imask = __shfl_sync(FULL, im_l, k);
-                if (!imask) continue;  // every tile pruned: nothing to add
                 const int gj = __shfl_sync(FULL, gj_l, k) + jb;
                 const float4 xj = sh.jx[wib][k][jb];
                 const float2 lj_j = sh.jl[wib][k][jb];
@@ -362,7 +361,6 @@ __device__ __forceinline__ void normal_items_x2(const Dev &d, int w0, int w1, in
             __syncwarp();
             for (int k = 0; k < ne; ++k) {
                 const unsigned imask = __shfl_sync(FULL, im_l, k);
-                if (!imask) continue;  // every tile pruned: nothing to add
                 const int gj = __shfl_sync(FULL, gj_l, k) + jb;
                 const unsigned lb = sh.lb[wib][k][lane];
                 touched |= imask;

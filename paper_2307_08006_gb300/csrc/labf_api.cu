@@ -454,30 +454,23 @@ int capture_graph(la_handle *h) {
         const cudaGraphNode_t *deps = nullptr;
         size_t nd = 0;
         CU(h, cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, nullptr, nullptr, nullptr));
-        cudaGraphConditionalHandle hc, hp;
+        cudaGraphConditionalHandle hc;
         CU(h, cudaGraphConditionalHandleCreate(&hc, cg, 0, cudaGraphCondAssignDefault));
-        CU(h, cudaGraphConditionalHandleCreate(&hp, cg, 0, cudaGraphCondAssignDefault));
-        launch_gate(h->d, 0, W, hc, hp, cs);
+        launch_gate(h->d, 0, W, hc, cs);
         CU(h, cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, &deps, nullptr, &nd));
-        // IF (some walker must rebuild) { list kernels }, then
-        // IF (some walker must prune, or rebuilt) { prune }
-        cudaGraphNode_t prev = nullptr;
-        for (int q = 0; q < 2; ++q) {
-            cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
-            p.conditional.handle = q == 0 ? hc : hp;
-            p.conditional.type = cudaGraphCondTypeIf;
-            p.conditional.size = 1;
-            cudaGraphNode_t cn;
-            if (q == 0) CU(h, cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &p));
-            else CU(h, cudaGraphAddNode(&cn, cg, &prev, nullptr, 1, &p));
-            cudaGraph_t body = p.conditional.phGraph_out[0];
-            CU(h, cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            if (q == 0) launch_rebuild(h->d, h->hv, 0, W, cb);
-            else launch_prune(h->d, h->hv, 0, W, cb);
-            cudaGraph_t body_out;
-            CU(h, cudaStreamEndCapture(cb, &body_out));
-            prev = cn;
-        }
+        // IF (some walker must rebuild or prune) { list kernels, pruning }
+        cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+        p.conditional.handle = hc;
+        p.conditional.type = cudaGraphCondTypeIf;
+        p.conditional.size = 1;
+        cudaGraphNode_t prev;
+        CU(h, cudaGraphAddNode(&prev, cg, deps, nullptr, nd, &p));
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        CU(h, cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        launch_rebuild(h->d, h->hv, 0, W, cb);
+        launch_prune(h->d, h->hv, 0, W, cb);
+        cudaGraph_t body_out;
+        CU(h, cudaStreamEndCapture(cb, &body_out));
         CU(h, cudaStreamUpdateCaptureDependencies(cs, &prev, nullptr, 1, cudaStreamSetCaptureDependencies));
         launch_pairs_fused(h->d, h->hv, (int)h->stages.size(), cs);
     }
@@ -486,7 +479,7 @@ int capture_graph(la_handle *h) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, LA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
     // graph steps: integrate, gate, fused pairs; list and prune kernels are
-    // counted per executed rebuild and pruning (device counters)
+    // counted per step that runs them (device counter)
     h->graph_launches_per_step = h->launches_per_step - rebuild_kernel_count(h->hv, 0, W) - 1 + 1;
     return LA_OK;
 }
@@ -731,7 +724,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         D.kT = S.kT;
         D.half_skin2 = (float)(0.25 * S.skin * S.skin);
         {
-            const double pm = h->opt.prune_margin == 0.0 ? S.skin / 3.0 : h->opt.prune_margin;
+            const double pm = h->opt.prune_margin;
             const bool on = pm > 0.0 && pm < S.skin;
             // a pruned tile holds no listed pair within r_c + pm; pruning is redone
             // once an atom moved 0.45 pm, so every pair moves less than 0.9 pm in
@@ -1409,7 +1402,7 @@ int la_stats(la_handle *h, int64_t *out, void *stream) {
         out[0] = h->steps;
         out[1] = (int64_t)c[0];
         // list kernels run inside the graph only on rebuild steps (counted by the gate)
-        out[2] = h->launches + (int64_t)c[6] * rebuild_kernel_count(h->hv, 0, h->L.W) + (int64_t)c[7];
+        out[2] = h->launches + (int64_t)c[6] * (rebuild_kernel_count(h->hv, 0, h->L.W) + 1);
         out[3] = (int64_t)c[1];
         out[4] = (int64_t)c[2];
         out[5] = ents;

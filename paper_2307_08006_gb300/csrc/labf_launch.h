@@ -23,8 +23,7 @@ void launch_integrate(const Dev &d, const HostView &hv, int w0, int w1, cudaStre
 void launch_finish(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
 void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
 void launch_items(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
-void launch_gate(const Dev &d, int w0, int w1, cudaGraphConditionalHandle handle,
-                 cudaGraphConditionalHandle handle_prune, cudaStream_t s);
+void launch_gate(const Dev &d, int w0, int w1, cudaGraphConditionalHandle handle, cudaStream_t s);
 void launch_prune(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
 int rebuild_kernel_count(const HostView &hv, int w0, int w1);
 void launch_pairs(const Dev &d, const HostView &hv, int w0, int w1, bool energy, cudaStream_t s);
