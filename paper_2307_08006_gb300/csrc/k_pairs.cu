@@ -165,7 +165,8 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
                 dst[1] = src[1];
             }
             __syncwarp();
-            for (int k = 0; k < ne; ++k) {
+            // one entry: every flagged i-cluster against the entry's j-cluster
+            auto entry = [&](int k) {
                 const unsigned imask = __shfl_sync(FULL, im_l, k);
                 const int gj = __shfl_sync(FULL, gj_l, k) + jb;
                 const float4 xj = sh.jx[wib][k][jb];
@@ -207,7 +208,15 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
                     }
                 }
                 flush_j(d, gj, ia, fj[0][0] + fj[1][0], fj[0][1] + fj[1][1], fj[0][2] + fj[1][2]);
+            };
+            // two entries per iteration: the compiler interleaves their
+            // independent loads and arithmetic (the order of every sum stays)
+            int k = 0;
+            for (; k + 1 < ne; k += 2) {
+                entry(k);
+                entry(k + 1);
             }
+            if (k < ne) entry(k);
             flush_i(d, gS, ia, jb, touched, fi);  // every 32 entries (EPC)
             touched = 0;
         }
@@ -359,7 +368,7 @@ __device__ __forceinline__ void normal_items_x2(const Dev &d, int w0, int w1, in
                 dst[1] = src[1];
             }
             __syncwarp();
-            for (int k = 0; k < ne; ++k) {
+            auto entry = [&](int k) {
                 const unsigned imask = __shfl_sync(FULL, im_l, k);
                 const int gj = __shfl_sync(FULL, gj_l, k) + jb;
                 const unsigned lb = sh.lb[wib][k][lane];
@@ -406,7 +415,13 @@ __device__ __forceinline__ void normal_items_x2(const Dev &d, int w0, int w1, in
                 }
                 const float2 jx = upk(fjx), jy = upk(fjy), jz = upk(fjz);
                 flush_j(d, gj, ia, jx.x + jx.y, jy.x + jy.y, jz.x + jz.y);
+            };
+            int k = 0;
+            for (; k + 1 < ne; k += 2) {
+                entry(k);
+                entry(k + 1);
             }
+            if (k < ne) entry(k);
             // flush the i-forces at the same 32-entry boundaries as the scalar variants
             if (((eb - it.y) & 31) == 32 - EPC2 || eb + EPC2 >= it.z) {
                 float fs[NIC][3];
