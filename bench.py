@@ -379,13 +379,14 @@ def gpu_arm(args):
             gpu_launches=launches,
             roofline=dict(bound="alu", achieved=achieved, peak=peak_tflops, unit="TFLOP/s",
                           frac=achieved / peak_tflops, traffic=traffic, traffic_source=traffic_src,
-                          kernel="k_pairs (normal + alchemical pairs)",
+                          kernel="k_pairs, fused step launch (normal + alchemical pairs, bonded, walker, lambda)",
                           pair_kernel_ms=pair_ms,
                           peak_note=f"{n_sm} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
                           kernel_ms=dict((k, v[0]) for k, v in kt.items()),
-                          timing_note="per-kernel CUDA events on the engine stream over --profile-steps "
-                                      "steps of the one-launch-per-task form, right after the timed region "
-                                      "(kernel nodes of the graph cannot be timed one by one)"),
+                          timing_note="CUDA events on the engine stream between the launches of the batched "
+                                      "step (integrate | list kernels + pruning | fused pair launch with bonded, "
+                                      "walker and lambda work) over --profile-steps steps, right after the timed "
+                                      "region (kernel nodes of the graph cannot be timed one by one)"),
             roofline_hbm=dict(bound="hbm", kernel="k_integrate", achieved=integ_gbs, peak=hbm_peak,
                               unit="GB/s", frac=integ_gbs / hbm_peak, bytes_per_launch=integ_bytes,
                               peak_source=hbm_src),
