@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -489,6 +490,11 @@ void set_pair_blocks(la_handle *h, int ctas_per_sm) {
 }
 
 // autotuner results per (device, system shape): CTAs/SM, entries/item, variant
+std::mutex &tune_mutex() {  // handles may be created from several host threads
+    static std::mutex m;
+    return m;
+}
+
 std::map<std::string, std::array<int, 3>> &tune_cache() {
     static std::map<std::string, std::array<int, 3>> c;
     return c;
@@ -542,13 +548,19 @@ int tune_pairs(la_handle *h, cudaStream_t s, bool use_cache) {
     char key[256];
     snprintf(key, sizeof key, "dev%d-sm%d-W%d-slots%lld-ent%d", h->dev, h->n_sm, h->L.W, h->L.slots,
              h->L.ent_cap);
-    auto it = tune_cache().find(key);
     int best_c = 4, best_k = h->L.chunk, best_m = 0;
-    if (use_cache && it != tune_cache().end()) {
-        best_c = it->second[0];
-        best_k = it->second[1];
-        best_m = it->second[2];
-    } else {
+    bool cached = false;
+    if (use_cache) {
+        std::lock_guard<std::mutex> lock(tune_mutex());
+        auto it = tune_cache().find(key);
+        if (it != tune_cache().end()) {
+            best_c = it->second[0];
+            best_k = it->second[1];
+            best_m = it->second[2];
+            cached = true;
+        }
+    }
+    if (!cached) {
         const int W = h->L.W;
         float best = 1e30f;
         const int ctas[] = {2, 3, 4, 6, 8};
@@ -583,6 +595,7 @@ int tune_pairs(la_handle *h, cudaStream_t s, bool use_cache) {
         }
         cudaEventDestroy(a);
         cudaEventDestroy(b);
+        std::lock_guard<std::mutex> lock(tune_mutex());
         tune_cache()[key] = {best_c, best_k, best_m};
     }
     h->hv.pair_variant = best_m;
