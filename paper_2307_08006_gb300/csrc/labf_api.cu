@@ -1451,7 +1451,7 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
         cudaEventRecord(ev[5], s);
         cudaEventRecord(ev[6], s);
         CU(h, cudaEventSynchronize(ev[6]));
-        for (int q = 0; q < LA_N_KERNELS; ++q) {
+        for (int q = 0; q < 3; ++q) {  // bonded, walker, lambda: inside the pair launch
             float ms = 0.f;
             cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
             acc[q] += ms;
