@@ -1432,7 +1432,7 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
     rc = flush_dirty(h, s);
     if (rc != LA_OK) return rc;
     const int W = h->L.W;
-    cudaEvent_t ev[LA_N_KERNELS + 1];
+    cudaEvent_t ev[4];  // integrate | list kernels + pruning | fused pair launch
     for (auto &e : ev) CU(h, cudaEventCreate(&e));
     double acc[LA_N_KERNELS] = {0};
     int64_t cnt[LA_N_KERNELS] = {0};
@@ -1447,11 +1447,8 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
         // terms and the lambda update
         launch_pairs_fused(h->d, h->hv, (int)h->stages.size(), s);
         cudaEventRecord(ev[3], s);
-        cudaEventRecord(ev[4], s);
-        cudaEventRecord(ev[5], s);
-        cudaEventRecord(ev[6], s);
-        CU(h, cudaEventSynchronize(ev[6]));
-        for (int q = 0; q < 3; ++q) {  // bonded, walker, lambda: inside the pair launch
+        CU(h, cudaEventSynchronize(ev[3]));
+        for (int q = 0; q < 3; ++q) {  // bonded, walker, lambda run inside the pair launch: 0
             float ms = 0.f;
             cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
             acc[q] += ms;
