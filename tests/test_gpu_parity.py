@@ -97,6 +97,21 @@ def test_forces_energies_dudl_water(lam0):
         check_forces(eng, sp, st, w)
 
 
+@pytest.mark.parametrize("n,m", [(2, 1), (1, 2), (2, 2)])
+def test_softcore_powers(n, m):
+    """Soft-core exponents other than the default (Sec. 3.1.2): forces, energy
+    terms, dU/dlambda and the theta derivatives against the oracle."""
+    sp = synth.with_changes(small_water(jitter=0.01), sc_n=n, sc_m=m)
+    run = synth.water_run(walkers_per_stage=2, n_bins=20)
+    eng, st = make_engine(sp, run, lam0=[0.02, 0.21, 0.44, 0.5])
+    osys = oracle.OracleSystem(sp)
+    for w in range(run.n_walkers):
+        g, ref = check_forces(eng, sp, st, w)
+        for key in ("dth", "d2th"):
+            scale = max(1.0, float(np.abs(ref[key]).max()))
+            np.testing.assert_allclose(g[key], ref[key], rtol=1e-4, atol=1e-5 * scale)
+
+
 def test_forces_lj_fluid():
     sp = synth.lj_fluid()
     run = synth.lj_fluid_run(n_walkers=4)

@@ -118,15 +118,17 @@ def test_softcore_vanishes_at_zero_coupling():
     np.testing.assert_allclose(r0["F"][:-1], rf["F"][:-1], rtol=1e-12, atol=1e-12)
 
 
-def test_softcore_finite_at_overlap():
-    # at lambda_v < 1 the soft-core energy stays finite at r = 0 (Sec. 3.1.2)
+@pytest.mark.parametrize("n,m", [(1, 1), (2, 1), (1, 2), (2, 2)])
+def test_softcore_finite_at_overlap(n, m):
+    # at lambda_v < 1 the soft-core energy stays finite at r = 0 (Sec. 3.1.2):
+    # with sigma = eps = 1 it tends to lambda^n 4 (1/s^2 - 1/s), s = alpha (1-lambda)^m
     for lv in (0.1, 0.5, 0.9):
-        sp = _two_atoms(1e-4, alch=(1, 0))
+        sp = synth.with_changes(_two_atoms(1e-4, alch=(1, 0)), sc_n=n, sc_m=m)
         o = oracle.OracleSystem(sp)
         res = oracle.energy_forces(o, sp.x.astype(np.float64), lv)
         alpha = 0.5
-        s = alpha * (1 - lv)
-        assert res["terms"][2] == pytest.approx(lv * 4 * (1 / s ** 2 - 1 / s), rel=1e-6)
+        s = alpha * (1 - lv) ** m
+        assert res["terms"][2] == pytest.approx(lv ** n * 4 * (1 / s ** 2 - 1 / s), rel=1e-6)
 
 
 def test_reaction_field_closed_forms():
@@ -183,9 +185,11 @@ def _restrained_small(seed=4):
     return sp, x
 
 
-@pytest.mark.parametrize("lam", [0.12, 0.37, 0.63, 0.91])
-def test_forces_match_finite_differences(lam):
+@pytest.mark.parametrize("lam,n,m", [(0.12, 1, 1), (0.37, 1, 1), (0.63, 1, 1), (0.91, 1, 1),
+                                     (0.37, 2, 2), (0.63, 2, 1)])
+def test_forces_match_finite_differences(lam, n, m):
     sp, x = _restrained_small()
+    sp = synth.with_changes(sp, sc_n=n, sc_m=m)
     o = oracle.OracleSystem(sp)
     res = oracle.energy_forces(o, x, lam)
     rng = np.random.default_rng(11)
@@ -200,17 +204,21 @@ def test_forces_match_finite_differences(lam):
 
 
 @pytest.mark.parametrize("lam", [0.05, 0.2, 0.45, 0.55, 0.8, 0.97])
-def test_dudl_matches_finite_differences(lam):
+@pytest.mark.parametrize("n,m", [(1, 1), (2, 1), (1, 2), (2, 2)])
+def test_dudl_matches_finite_differences(lam, n, m):
+    # every soft-core power pair (n, m) of Sec. 3.1.2, not only the default
     sp, x = _restrained_small()
+    sp = synth.with_changes(sp, sc_n=n, sc_m=m)
     o = oracle.OracleSystem(sp)
     h = 1e-6
     fd = (oracle.energy_forces(o, x, lam + h)["U"] - oracle.energy_forces(o, x, lam - h)["U"]) / (2 * h)
     assert oracle.energy_forces(o, x, lam)["dUdl"] == pytest.approx(fd, rel=1e-6, abs=1e-4)
 
 
-@pytest.mark.parametrize("lam", [0.2, 0.45, 0.7])
-def test_theta_derivatives_match_finite_differences(lam):
+@pytest.mark.parametrize("lam,n,m", [(0.2, 1, 1), (0.45, 1, 1), (0.7, 1, 1), (0.45, 2, 2)])
+def test_theta_derivatives_match_finite_differences(lam, n, m):
     sp, x = _restrained_small()
+    sp = synth.with_changes(sp, sc_n=n, sc_m=m)
     o = oracle.OracleSystem(sp)
     res = oracle.energy_forces(o, x, lam)
     alch = np.nonzero(sp.alch)[0]
