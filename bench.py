@@ -36,17 +36,24 @@ if ROOT not in sys.path:
 METRIC = "aggregate walker-ns/day"
 UNIT = "walker-ns/day"
 FLOP_PER_PAIR = 37  # FP32 flops per in-cutoff LJ+RF pair, force only (FMA = 2); see k_pairs.cu
-WORKLOAD = ("solvation-like: 4096 flexible 3-site waters + 12-site alchemical solute "
-            "(12300 atoms, 5 nm box, RF eps_rf=78, r_c=1.0 nm, list skin 0.15 nm), 16 walkers "
+SKIN_NM = 0.15  # list radius r_c + skin
+PRUNE_NM = 0.05  # pair-pass pruning margin (0: off); measured best with SKIN_NM
+
+
+def workload_name(skin=SKIN_NM, prune=PRUNE_NM):
+    return ("solvation-like: 4096 flexible 3-site waters + 12-site alchemical solute "
+            f"(12300 atoms, 5 nm box, RF eps_rf=78, r_c=1.0 nm, list skin {skin:g} nm, "
+            f"pruning margin {prune:g} nm), 16 walkers "
             "(8 vdW-stage on [0,0.5] + 8 Coulomb-stage on [0.5,1]), 100 bins per stage, dt=1 fs, 300 K")
 
 
-def workload():
+
+
+def workload(skin=SKIN_NM):
     from paper_2307_08006_gb300 import synth
 
     spec = synth.water_box(4096, 12, seed=8007)
-    # list radius r_c + 0.15 nm: measured optimum of list size vs rebuild rate
-    run = synth.water_run(seed=8007, walkers_per_stage=8, n_bins=100, n_full=200.0, skin=0.15)
+    run = synth.water_run(seed=8007, walkers_per_stage=8, n_bins=100, n_full=200.0, skin=skin)
     return spec, run
 
 
@@ -102,14 +109,14 @@ def reference_arm(args):
             steps_total += 1
             secs_total += dt
             cb = cbk
-    spec, run = workload()
+    spec, run = workload(args.skin)
     val = walker_ns_per_day(run.n_walkers, steps_total, run.dt, secs_total)
     cb["value"] = val
     line = dict(impl="reference", metric=METRIC, value=val, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * secs_total / max(steps_total, 1),
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=WORKLOAD, walkers=run.n_walkers, atoms_per_walker=spec.n,
-                            md_steps_per_bench_step=1),
+                config=dict(workload=workload_name(args.skin, args.prune_margin), walkers=run.n_walkers,
+                            atoms_per_walker=spec.n, md_steps_per_bench_step=1),
                 cpu_baseline=cb, e2e=dict(value=val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
     return 0
@@ -213,9 +220,9 @@ def gpu_arm(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    spec, run = workload()
+    spec, run = workload(args.skin)
     state = synth.initial_state(spec, run, seed=run.seed + 1000 * rank)
-    opts = dict(graph_steps=args.graph_steps, autotune=int(args.autotune))
+    opts = dict(graph_steps=args.graph_steps, autotune=int(args.autotune), prune_margin=args.prune_margin)
     if args.launch:  # a fixed pair-kernel launch shape instead of the tuner's
         for kv in args.launch.split(","):
             k, v = kv.split("=")
@@ -359,8 +366,8 @@ def gpu_arm(args):
             metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
             ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
             dtype="f32", data="synthetic",
-            config=dict(workload=WORKLOAD, walkers=run.n_walkers, atoms_per_walker=spec.n,
-                        md_steps_per_bench_step=md, l2="flushed between bench steps (256 MB write)",
+            config=dict(workload=workload_name(args.skin, args.prune_margin), walkers=run.n_walkers,
+                        atoms_per_walker=spec.n, md_steps_per_bench_step=md, l2="flushed between bench steps (256 MB write)",
                         parallelism="replicas" if world > 1 else "1 GPU, walkers batched",
                         launch=eng.autotune_report(),
                         launch_options=",".join(
@@ -384,7 +391,7 @@ def gpu_arm(args):
                           peak_note=f"{n_sm} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
                           kernel_ms=dict((k, v[0]) for k, v in kt.items()),
                           timing_note="CUDA events on the engine stream between the launches of the batched "
-                                      "step (integrate | list kernels + pruning | fused pair launch with bonded, "
+                                      "step (integrate | gate + list kernels | fused pair launch with bonded, "
                                       "walker and lambda work) over --profile-steps steps, right after the timed "
                                       "region (kernel nodes of the graph cannot be timed one by one)"),
             roofline_hbm=dict(bound="hbm", kernel="k_integrate", achieved=integ_gbs, peak=hbm_peak,
@@ -417,6 +424,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--launch", default="",
                     help="fixed pair-kernel shape, e.g. pair_variant=1,pair_ctas_per_sm=6,chunk_entries=64")
+    ap.add_argument("--skin", type=float, default=SKIN_NM, help="list skin (nm)")
+    ap.add_argument("--prune-margin", type=float, default=PRUNE_NM,
+                    help="pair-pass pruning margin (nm); 0 = off")
     ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
     args = ap.parse_args()
     os.makedirs(args.out_dir, exist_ok=True)

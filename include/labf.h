@@ -155,8 +155,11 @@ typedef struct {
                                     32 (0 = 32) */
     double prune_margin;         /* dynamic pruning of the batched step: tiles with no
                                     listed pair within r_cut + prune_margin are skipped
-                                    until some atom moves 0.45 prune_margin (then they
-                                    are re-pruned); 0 (default), < 0 or >= skin = off.
+                                    until some atom of the system has moved 0.45
+                                    prune_margin; then the next batched pair pass
+                                    evaluates the listed tiles of all its walkers and
+                                    prunes them again (so does the pass after a list
+                                    rebuild).  0 (default), < 0 or >= skin = off.
                                     Results are identical either way. */
 } la_options;
 
@@ -343,7 +346,7 @@ int la_stats(la_handle *h, int64_t *out, void *stream);
  * and the lambda update run inside the pair launch, so their classes read 0
  * and "pairs" is the whole fused launch.  Synchronising.
  */
-#define LA_N_KERNELS 6 /* integrate, rebuild (list kernels + pruning), pairs, bonded, walker, lambda */
+#define LA_N_KERNELS 6 /* integrate, rebuild (gate + list kernels), pairs, bonded, walker, lambda */
 int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_out, void *stream);
 
 /*

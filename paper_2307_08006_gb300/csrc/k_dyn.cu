@@ -59,7 +59,8 @@ __global__ void k_integrate(Dev d, int w0, int w1, int g0, int g1) {
         const unsigned long long f0 = Fp[0], f1 = Fp[1], f2 = Fp[2];
         const float2 im = d.im[g];
         float4 v = d.vv[g];
-        float4 x = d.xq[g];
+        const float4 x0 = d.xq[g];
+        float4 x = x0;
         const float4 r = d.xref[g];
         if (a < 0) continue;
         const WalkerDev &W = d.walk[w];
@@ -108,9 +109,20 @@ __global__ void k_integrate(Dev d, int w0, int w1, int g0, int g1) {
         // then run once, fully parallel, instead of on most steps
         if (dx * dx + dy * dy + dz * dz > S.half_skin2)
             for (int k = 0; k < S.w_count; ++k) d.rebuild[S.w_first + k] = 1;
-        // the same for the pruned tiles of the batched step
+        // the same for the pruned tiles of the batched step; all walkers of the
+        // system re-prune together, so that a pair launch runs either the
+        // pruning form of the item loop or the common one.  The positions this
+        // step starts from are the new reference when the previous step's pair
+        // pass re-pruned the walker (it ran with the step counter one below the
+        // current one).
         if (S.prune_disp2 > 0.f) {
-            const float4 rp = d.xprune[g];
+            float4 rp;
+            if (d.prune_now[w] == d.step[w]) {
+                rp = x0;
+                d.xprune[g] = x0;
+            } else {
+                rp = d.xprune[g];
+            }
             dx = min_image(x.x - rp.x, S.boxf, S.box_invf);
             dy = min_image(x.y - rp.y, S.boxf, S.box_invf);
             dz = min_image(x.z - rp.z, S.boxf, S.box_invf);

@@ -675,9 +675,11 @@ __global__ void __launch_bounds__(AL_WARPS * 32) k_alchlist(Dev d, int w0, int w
 
 // -------------------------------------------------------------------------
 // R10: pair-kernel work items (chunks of `chunk` entries of one
-// super-cluster), per walker; clears the rebuild flag.
+// super-cluster), per walker; clears the rebuild flag.  In the batched step
+// (prune_fresh) a walker with pruning on has its fresh list pruned by this
+// step's pair pass.
 // -------------------------------------------------------------------------
-__global__ void k_items(Dev d, int w0) {
+__global__ void k_items(Dev d, int w0, int prune_fresh) {
     const int w = w0 + blockIdx.x;
     if (!d.rebuild[w]) return;
     const WalkerDev &W = d.walk[w];
@@ -724,147 +726,46 @@ __global__ void k_items(Dev d, int w0) {
         if (carry > W.item_cap) set_status(d, LA_STATUS_LIST_OVERFLOW);
         d.n_items[w] = min(carry, W.item_cap);
         d.rebuild[w] = 0;
-        if (d.sys[W.sys].prune_disp2 > 0.f) d.prune[w] = 1;  // fresh lists: prune before the next batched pass
+        if (prune_fresh && d.sys[W.sys].prune_disp2 > 0.f) d.prune_now[w] = d.step[w] + 1ull;
         atomicAdd(&d.counters[0], 1ull);
     }
 }
 
 // -------------------------------------------------------------------------
-// gate of the rebuild chain inside a CUDA graph: one thread sets the step's
-// conditional handle to "some walker must rebuild or prune", so that the
-// graph skips the whole chain otherwise; such steps are counted in
-// counters[6]
+// gate of the batched step, after the integrator: a walker whose pruning was
+// requested is re-pruned by this step's pair pass (prune_now = 1 + step
+// counter; the next integrator step takes the positions it starts from as the
+// walker's new reference).  Inside a CUDA graph one thread also sets the
+// step's conditional handle to "some walker must rebuild", so that the graph
+// skips the list kernels otherwise; such steps are counted in counters[6].
 // -------------------------------------------------------------------------
-__global__ void k_gate(Dev d, int w0, int w1, cudaGraphConditionalHandle handle) {
+__global__ void k_gate(Dev d, int w0, int w1, cudaGraphConditionalHandle handle, int conditional) {
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
-    for (int w = w0 + threadIdx.x; w < w1; w += blockDim.x)
-        if (d.rebuild[w] | d.prune[w]) any = 1;
+    for (int w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+        const int p = d.prune[w];
+        d.prune_now[w] = p ? d.step[w] + 1ull : 0ull;
+        if (p) d.prune[w] = 0;
+        if (d.rebuild[w]) any = 1;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // the body (list kernels, then pruning) runs when some walker must
-        // rebuild or prune; every kernel in it skips walkers not flagged
+    if (conditional && threadIdx.x == 0) {
         cudaGraphSetConditional(handle, any ? 1u : 0u);
         if (any) atomicAdd(&d.counters[6], 1ull);
     }
 }
 
-void launch_gate(const Dev &d, int w0, int w1, cudaGraphConditionalHandle handle, cudaStream_t s) {
-    k_gate<<<1, 256, 0, s>>>(d, w0, w1, handle);
-}
-
-// -------------------------------------------------------------------------
-// R11: dynamic pruning of the batched step.  For every cluster-pair entry
-// of a flagged walker, each listed i-cluster (bits 16-23 of the header) is
-// kept in the pruned mask (bits 8-15) only if one of its listed atom pairs
-// is now within r_c + prune margin (FP32).  Until the next pruning no atom
-// moves more than 0.45 margin, so a skipped tile cannot reach the cutoff:
-// its pairs would add exact zeros, and results are identical with or
-// without pruning.  One warp per super-cluster; entries are staged 32 at a
-// time as in the pair kernel.  The positions become the new reference.
-// The last warp out clears the flags.
-// -------------------------------------------------------------------------
-constexpr int PR_WARPS = 4, CTR_PR_DONE = 10;
-
-__global__ void __launch_bounds__(PR_WARPS * 32) k_prune(Dev d, int w0, int w1) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int ia = lane & 7, jb = lane >> 3;
-    __shared__ float4 sxi[PR_WARPS][SC];
-    __shared__ float4 sxj[PR_WARPS][32][JC];
-    __shared__ unsigned char slb[PR_WARPS][32][32];
-    __shared__ unsigned skeep[PR_WARPS][32];
-    const int nwarp = gridDim.x * PR_WARPS;
-    const int s_begin = d.walk[w0].sc_off, s_end = d.walk[w1 - 1].sc_off + d.walk[w1 - 1].sc_cap;
-    for (int s = s_begin + blockIdx.x * PR_WARPS + wib; s < s_end; s += nwarp) {
-        int lo = w0, hi = w1 - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (d.walk[mid].sc_off <= s) lo = mid; else hi = mid - 1;
-        }
-        const int w = lo;
-        if (!d.prune[w]) continue;
-        const WalkerDev &W = d.walk[w];
-        const SysDev &S = d.sys[W.sys];
-        const int S_loc = s - W.sc_off;
-        const int gS = W.slot_off + S_loc * SC;
-        __syncwarp();
-        for (int k = lane; k < SC; k += 32) {
-            const float4 x = d.xq[gS + k];
-            sxi[wib][k] = x;
-            d.xprune[gS + k] = x;
-        }
-        if (S_loc >= d.n_sc[w] || S.prune_disp2 <= 0.f) continue;
-        __syncwarp();
-        const int ne = d.sc_nent[s];
-        const size_t ebase = (size_t)s * d.ent_cap;
-        const float L = S.boxf, rp2 = S.rprune2;
-        for (int eb = 0; eb < ne; eb += 32) {
-            const int nb = min(32, ne - eb);
-            int2 hdr = make_int2(0, 0);
-            __syncwarp();
-            if (lane < nb) {
-                hdr = d.ent_hdr[ebase + eb + lane];
-                const float sx = (float)((hdr.y & 3) - 1) * L;
-                const float sy = (float)(((hdr.y >> 2) & 3) - 1) * L;
-                const float sz = (float)(((hdr.y >> 4) & 3) - 1) * L;
-#pragma unroll
-                for (int q = 0; q < JC; ++q) {
-                    float4 x = d.xq[hdr.x + q];
-                    x.x += sx;
-                    x.y += sy;
-                    x.z += sz;
-                    sxj[wib][lane][q] = x;
-                }
-                const uint4 *src = reinterpret_cast<const uint4 *>(d.ent_lb + 32 * (ebase + eb + lane));
-                uint4 *dst = reinterpret_cast<uint4 *>(&slb[wib][lane][0]);
-                dst[0] = src[0];
-                dst[1] = src[1];
-            }
-            __syncwarp();
-            for (int k = 0; k < nb; ++k) {
-                const unsigned im0 = ((unsigned)__shfl_sync(0xffffffffu, hdr.y, k) >> 16) & 0xffu;
-                const float4 xj = sxj[wib][k][jb];
-                const unsigned lb = slb[wib][k][lane] & im0;
-                unsigned keep = 0;
-                for (unsigned m = lb; m; m &= m - 1u) {
-                    const int ic = __ffs(m) - 1;
-                    const float4 xi = sxi[wib][ic * IC + ia];
-                    const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-                    if (dx * dx + dy * dy + dz * dz < rp2) keep |= 1u << ic;
-                }
-                keep = __reduce_or_sync(0xffffffffu, keep);
-                if (lane == 0) skeep[wib][k] = keep;
-            }
-            __syncwarp();
-            if (lane < nb)
-                d.ent_hdr[ebase + eb + lane].y = (hdr.y & ~0xff00) | (int)(skeep[wib][lane] << 8);
-        }
-    }
-    if (lane == 0) {
-        __threadfence();
-        const unsigned long long done = atomicAdd(&d.counters[CTR_PR_DONE], 1ull);
-        if (done == (unsigned long long)gridDim.x * PR_WARPS - 1ull) {
-            for (int w = w0; w < w1; ++w) d.prune[w] = 0;
-            d.counters[CTR_PR_DONE] = 0ull;
-            __threadfence();
-        }
-    }
-}
-
-void launch_prune(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s) {
-    int nsc = 0;
-    for (int w = w0; w < w1; ++w) nsc += hv.sc_cap[w];
-    int blocks = (nsc + PR_WARPS - 1) / PR_WARPS;
-    blocks = blocks < 1 ? 1 : (blocks > hv.n_sm * 8 ? hv.n_sm * 8 : blocks);
-    k_prune<<<blocks, PR_WARPS * 32, 0, s>>>(d, w0, w1);
+void launch_gate(const Dev &d, int w0, int w1, cudaGraphConditionalHandle handle, bool conditional,
+                 cudaStream_t s) {
+    k_gate<<<1, 256, 0, s>>>(d, w0, w1, handle, conditional ? 1 : 0);
 }
 
 // -------------------------------------------------------------------------
 // host launcher of the whole rebuild chain (every kernel exits early for
 // walkers whose rebuild flag is clear)
 // -------------------------------------------------------------------------
-void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s) {
+void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s, bool batched) {
     const int g0 = hv.slot_off[w0], g1 = hv.slot_off[w1 - 1] + hv.slot_cap[w1 - 1];
     int sb = (g1 - g0 + 255) / 256;
     sb = sb < 1 ? 1 : (sb > hv.n_sm * 8 ? hv.n_sm * 8 : sb);
@@ -895,11 +796,11 @@ void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream
         ab = ab > hv.n_sm * 8 ? hv.n_sm * 8 : ab;
         k_alchlist<<<ab, AL_WARPS * 32, 0, s>>>(d, w0, w1, a0, a1);
     }
-    k_items<<<nw, 256, 0, s>>>(d, w0);
+    k_items<<<nw, 256, 0, s>>>(d, w0, batched ? 1 : 0);
 }
 
 void launch_items(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s) {
-    k_items<<<w1 - w0, 256, 0, s>>>(d, w0);
+    k_items<<<w1 - w0, 256, 0, s>>>(d, w0, 0);
 }
 
 int rebuild_kernel_count(const HostView &hv, int w0, int w1) {

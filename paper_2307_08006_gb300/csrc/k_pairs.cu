@@ -100,12 +100,134 @@ __device__ __forceinline__ void flush_j(const Dev &d, int gj, int ia, float fjx,
         atomicAdd(d.F + 3 * (size_t)gj + (ia >> 1), (unsigned long long)__float2ll_rn(-c * F_TO_FIX));
 }
 
-// MSHIFT: 8 reads the i-cluster mask pruned for the batched step, 16 the
-// listed one (one-task launches, which run without pruning)
+// One work item's entries, prepared and evaluated 32 at a time; the
+// i-forces are flushed after every 32 entries.  MSHIFT: 8 reads the i-cluster
+// mask pruned for the batched step, 16 the listed one (one-task launches,
+// which run without pruning).  PRUNE (batched step, walker due for
+// re-pruning): the listed mask is evaluated and each entry's pruned mask is
+// rewritten with the i-clusters holding a listed pair within r_c + margin (a
+// ballot per tile), which later steps read; every tile that is skipped adds
+// exact zeros, so results do not depend on the pruning.
+template <bool ENERGY, int WARPS, int MSHIFT, bool PRUNE>
+__device__ __forceinline__ void item_entries(const Dev &d, PairShared<WARPS> &sh, const SysDev &S, int4 it, int gS,
+                                             float &elj, float &erf, int &npair) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int ia = lane & 7, jb = lane >> 3;
+    const float L = S.boxf, rc2 = S.rc2, krf2 = 2.0f * S.krf, krf = S.krf, crf = S.crf;
+    const float rp2 = S.rprune2;
+    float fi[NIC][3];
+#pragma unroll
+    for (int ic = 0; ic < NIC; ++ic) fi[ic][0] = fi[ic][1] = fi[ic][2] = 0.f;
+    unsigned touched = 0;
+    const size_t ebase = (size_t)it.x * d.ent_cap;
+    for (int eb = it.y; eb < it.z; eb += EPC) {
+        const int ne = min(EPC, it.z - eb);
+        // prepare up to 32 entries, one per lane
+        int gj_l = 0, hy_l = 0;
+        unsigned im_l = 0, keep_l = 0;
+        __syncwarp();
+        if (lane < ne) {
+            const int2 hdr = d.ent_hdr[ebase + eb + lane];
+            gj_l = hdr.x;
+            hy_l = hdr.y;
+            im_l = ((unsigned)hdr.y >> (PRUNE ? 16 : MSHIFT)) & 0xffu;
+            const float sx = (float)((hdr.y & 3) - 1) * L;
+            const float sy = (float)(((hdr.y >> 2) & 3) - 1) * L;
+            const float sz = (float)(((hdr.y >> 4) & 3) - 1) * L;
+#pragma unroll
+            for (int q = 0; q < JC; ++q) {
+                float4 x = d.xq[gj_l + q];
+                x.x += sx;
+                x.y += sy;
+                x.z += sz;
+                sh.jx[wib][lane][q] = x;
+                sh.jl[wib][lane][q] = d.lj[gj_l + q];
+            }
+            const uint4 *src = reinterpret_cast<const uint4 *>(d.ent_lb + 32 * (ebase + eb + lane));
+            uint4 *dst = reinterpret_cast<uint4 *>(&sh.lb[wib][lane][0]);
+            dst[0] = src[0];
+            dst[1] = src[1];
+        }
+        __syncwarp();
+        // one entry: every flagged i-cluster against the entry's j-cluster
+        auto entry = [&](int k) {
+            const unsigned imask = __shfl_sync(FULL, im_l, k);
+            const int gj = __shfl_sync(FULL, gj_l, k) + jb;
+            const float4 xj = sh.jx[wib][k][jb];
+            const float2 lj_j = sh.jl[wib][k][jb];
+            const unsigned lb = sh.lb[wib][k][lane];
+            touched |= imask;
+            float fj[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};  // even, odd i-clusters
+            unsigned kb = 0;  // this lane's pairs within r_c + margin, per i-cluster
+#pragma unroll
+            for (int ic = 0; ic < NIC; ++ic) {
+                if (imask & (1u << ic)) {
+                    const float4 xi = sh.sxq[wib][ic * IC + ia];
+                    const float2 li = sh.slj[wib][ic * IC + ia];
+                    const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (PRUNE) kb |= ((lb & (1u << ic)) && r2 < rp2) ? 1u << ic : 0u;
+                    const bool in = (lb & (1u << ic)) && (r2 < rc2);
+                    const float rinv = rsqrtf(r2);
+                    const float r2inv = rinv * rinv;
+                    const float sg = li.x + lj_j.x;
+                    const float sr2 = sg * sg * r2inv;
+                    const float sr6 = sr2 * sr2 * sr2;
+                    const float e4s6 = li.y * lj_j.y * sr6;
+                    const float qq = xi.w * xj.w;
+                    const float b = fmaf(qq, rinv, e4s6 * fmaf(12.f, sr6, -6.f));
+                    float fs = fmaf(b, r2inv, -qq * krf2);
+                    fs = in ? fs : 0.f;
+                    fi[ic][0] = fmaf(fs, dx, fi[ic][0]);
+                    fi[ic][1] = fmaf(fs, dy, fi[ic][1]);
+                    fi[ic][2] = fmaf(fs, dz, fi[ic][2]);
+                    fj[ic & 1][0] = fmaf(fs, dx, fj[ic & 1][0]);
+                    fj[ic & 1][1] = fmaf(fs, dy, fj[ic & 1][1]);
+                    fj[ic & 1][2] = fmaf(fs, dz, fj[ic & 1][2]);
+                    if (ENERGY) {
+                        if (in) {
+                            elj += e4s6 * (sr6 - 1.f);
+                            erf += qq * (rinv + krf * r2 - crf);
+                            ++npair;
+                        }
+                    }
+                }
+            }
+            if (PRUNE) {
+                const unsigned keep = __reduce_or_sync(FULL, kb);
+                keep_l = lane == k ? keep : keep_l;
+            }
+            flush_j(d, gj, ia, fj[0][0] + fj[1][0], fj[0][1] + fj[1][1], fj[0][2] + fj[1][2]);
+        };
+        // two entries per iteration: the compiler interleaves their
+        // independent loads and arithmetic (the order of every sum stays);
+        // the pruning form, which holds more registers, takes one
+        int k = 0;
+        if (!PRUNE)
+            for (; k + 1 < ne; k += 2) {
+                entry(k);
+                entry(k + 1);
+            }
+        for (; k < ne; ++k) entry(k);
+        flush_i(d, gS, ia, jb, touched, fi);  // every 32 entries (EPC)
+        touched = 0;
+        if (PRUNE && lane < ne) d.ent_hdr[ebase + eb + lane].y = (hy_l & ~0xff00) | (int)(keep_l << 8);
+    }
+}
+
+// the re-pruning form, out of line: the common form's code stays as it is
+template <int WARPS>
+__device__ __noinline__ void item_entries_prune(const Dev &d, PairShared<WARPS> &sh, const SysDev &S, int4 it,
+                                                int gS) {
+    float elj = 0.f, erf = 0.f;
+    int npair = 0;
+    item_entries<false, WARPS, 8, true>(d, sh, S, it, gS, elj, erf, npair);
+}
+
+// work items of the normal pairs, handed out by a global counter
 template <bool ENERGY, int WARPS, int MSHIFT>
 __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int nblk, PairShared<WARPS> &sh) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int ia = lane & 7, jb = lane >> 3;
     const int nw = w1 - w0;
     const int total = sh.pre[nw];
     for (;;) {
@@ -129,97 +251,10 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
         sh.sxq[wib][lane + 32] = d.xq[gS + lane + 32];
         sh.slj[wib][lane] = d.lj[gS + lane];
         sh.slj[wib][lane + 32] = d.lj[gS + lane + 32];
-        const float L = S.boxf, rc2 = S.rc2, krf2 = 2.0f * S.krf, krf = S.krf, crf = S.crf;
-        float fi[NIC][3];
-#pragma unroll
-        for (int ic = 0; ic < NIC; ++ic) fi[ic][0] = fi[ic][1] = fi[ic][2] = 0.f;
-        unsigned touched = 0;
         float elj = 0.f, erf = 0.f;
         int npair = 0;
-        const size_t ebase = (size_t)sc * d.ent_cap;
-        for (int eb = it.y; eb < it.z; eb += EPC) {
-            const int ne = min(EPC, it.z - eb);
-            // prepare up to 32 entries, one per lane
-            int gj_l = 0;
-            unsigned im_l = 0;
-            __syncwarp();
-            if (lane < ne) {
-                const int2 hdr = d.ent_hdr[ebase + eb + lane];
-                gj_l = hdr.x;
-                im_l = ((unsigned)hdr.y >> MSHIFT) & 0xffu;
-                const float sx = (float)((hdr.y & 3) - 1) * L;
-                const float sy = (float)(((hdr.y >> 2) & 3) - 1) * L;
-                const float sz = (float)(((hdr.y >> 4) & 3) - 1) * L;
-#pragma unroll
-                for (int q = 0; q < JC; ++q) {
-                    float4 x = d.xq[gj_l + q];
-                    x.x += sx;
-                    x.y += sy;
-                    x.z += sz;
-                    sh.jx[wib][lane][q] = x;
-                    sh.jl[wib][lane][q] = d.lj[gj_l + q];
-                }
-                const uint4 *src = reinterpret_cast<const uint4 *>(d.ent_lb + 32 * (ebase + eb + lane));
-                uint4 *dst = reinterpret_cast<uint4 *>(&sh.lb[wib][lane][0]);
-                dst[0] = src[0];
-                dst[1] = src[1];
-            }
-            __syncwarp();
-            // one entry: every flagged i-cluster against the entry's j-cluster
-            auto entry = [&](int k) {
-                const unsigned imask = __shfl_sync(FULL, im_l, k);
-                const int gj = __shfl_sync(FULL, gj_l, k) + jb;
-                const float4 xj = sh.jx[wib][k][jb];
-                const float2 lj_j = sh.jl[wib][k][jb];
-                const unsigned lb = sh.lb[wib][k][lane];
-                touched |= imask;
-                float fj[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};  // even, odd i-clusters
-#pragma unroll
-                for (int ic = 0; ic < NIC; ++ic) {
-                    if (imask & (1u << ic)) {
-                        const float4 xi = sh.sxq[wib][ic * IC + ia];
-                        const float2 li = sh.slj[wib][ic * IC + ia];
-                        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const bool in = (lb & (1u << ic)) && (r2 < rc2);
-                        const float rinv = rsqrtf(r2);
-                        const float r2inv = rinv * rinv;
-                        const float sg = li.x + lj_j.x;
-                        const float sr2 = sg * sg * r2inv;
-                        const float sr6 = sr2 * sr2 * sr2;
-                        const float e4s6 = li.y * lj_j.y * sr6;
-                        const float qq = xi.w * xj.w;
-                        const float b = fmaf(qq, rinv, e4s6 * fmaf(12.f, sr6, -6.f));
-                        float fs = fmaf(b, r2inv, -qq * krf2);
-                        fs = in ? fs : 0.f;
-                        fi[ic][0] = fmaf(fs, dx, fi[ic][0]);
-                        fi[ic][1] = fmaf(fs, dy, fi[ic][1]);
-                        fi[ic][2] = fmaf(fs, dz, fi[ic][2]);
-                        fj[ic & 1][0] = fmaf(fs, dx, fj[ic & 1][0]);
-                        fj[ic & 1][1] = fmaf(fs, dy, fj[ic & 1][1]);
-                        fj[ic & 1][2] = fmaf(fs, dz, fj[ic & 1][2]);
-                        if (ENERGY) {
-                            if (in) {
-                                elj += e4s6 * (sr6 - 1.f);
-                                erf += qq * (rinv + krf * r2 - crf);
-                                ++npair;
-                            }
-                        }
-                    }
-                }
-                flush_j(d, gj, ia, fj[0][0] + fj[1][0], fj[0][1] + fj[1][1], fj[0][2] + fj[1][2]);
-            };
-            // two entries per iteration: the compiler interleaves their
-            // independent loads and arithmetic (the order of every sum stays)
-            int k = 0;
-            for (; k + 1 < ne; k += 2) {
-                entry(k);
-                entry(k + 1);
-            }
-            if (k < ne) entry(k);
-            flush_i(d, gS, ia, jb, touched, fi);  // every 32 entries (EPC)
-            touched = 0;
-        }
+        if (MSHIFT == 8 && d.prune_now[w] != 0ull) item_entries_prune<WARPS>(d, sh, S, it, gS);
+        else item_entries<ENERGY, WARPS, MSHIFT, false>(d, sh, S, it, gS, elj, erf, npair);
         if (ENERGY) {
             const double el = warp_sum((double)elj), er = warp_sum((double)erf);
             int np = npair;
@@ -295,10 +330,141 @@ struct PairShared2 {
     int pre[LA_MAX_WALKERS_PER_LAUNCH + 1];
 };
 
+// one work item of the packed form (PRUNE as in item_entries)
+template <int WARPS, int MSHIFT, bool PRUNE>
+__device__ __forceinline__ void item_entries_x2(const Dev &d, PairShared2<WARPS> &sh, const SysDev &S, int4 it,
+                                                int gS) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int ia = lane & 7, jb = lane >> 3;
+    const float L = S.boxf, rc2 = S.rc2, rp2 = S.rprune2;
+    const f32x2 nkrf2 = pk(-2.0f * S.krf, -2.0f * S.krf);
+    f32x2 fi[NIC / 2][3];
+#pragma unroll
+    for (int p = 0; p < NIC / 2; ++p) fi[p][0] = fi[p][1] = fi[p][2] = 0ull;
+    unsigned touched = 0;
+    const size_t ebase = (size_t)it.x * d.ent_cap;
+    for (int eb = it.y; eb < it.z; eb += EPC2) {
+        const int ne = min(EPC2, it.z - eb);
+        int gj_l = 0, hy_l = 0;
+        unsigned im_l = 0, keep_l = 0;
+        __syncwarp();
+        if (lane < ne) {
+            const int2 hdr = d.ent_hdr[ebase + eb + lane];
+            gj_l = hdr.x;
+            hy_l = hdr.y;
+            im_l = ((unsigned)hdr.y >> (PRUNE ? 16 : MSHIFT)) & 0xffu;
+            const float sx = (float)((hdr.y & 3) - 1) * L;
+            const float sy = (float)(((hdr.y >> 2) & 3) - 1) * L;
+            const float sz = (float)(((hdr.y >> 4) & 3) - 1) * L;
+#pragma unroll
+            for (int q = 0; q < JC; ++q) {
+                float4 x = d.xq[gj_l + q];
+                const float2 l = d.lj[gj_l + q];
+                x.x += sx;
+                x.y += sy;
+                x.z += sz;
+                sh.sj[wib][lane][q][0] = make_float4(x.x, x.x, x.y, x.y);
+                sh.sj[wib][lane][q][1] = make_float4(x.z, x.z, x.w, x.w);
+                sh.sj[wib][lane][q][2] = make_float4(l.x, l.x, l.y, l.y);
+            }
+            const uint4 *src = reinterpret_cast<const uint4 *>(d.ent_lb + 32 * (ebase + eb + lane));
+            uint4 *dst = reinterpret_cast<uint4 *>(&sh.lb[wib][lane][0]);
+            dst[0] = src[0];
+            dst[1] = src[1];
+        }
+        __syncwarp();
+        auto entry = [&](int k) {
+            const unsigned imask = __shfl_sync(FULL, im_l, k);
+            const int gj = __shfl_sync(FULL, gj_l, k) + jb;
+            const unsigned lb = sh.lb[wib][k][lane];
+            touched |= imask;
+            f32x2 fjx = 0ull, fjy = 0ull, fjz = 0ull;  // (even, odd) i-clusters
+            unsigned kb = 0;  // this lane's pairs within r_c + margin, per i-cluster
+#pragma unroll
+            for (int p = 0; p < NIC / 2; ++p) {
+                if (imask & (3u << (2 * p))) {
+                    const float4 I0 = sh.si[wib][p][ia][0], I1 = sh.si[wib][p][ia][1];
+                    const float4 I2 = sh.si[wib][p][ia][2];
+                    // j operands re-read per i-cluster pair: keeps 12 registers free
+                    const float4 J0 = sh.sj[wib][k][jb][0], J1 = sh.sj[wib][k][jb][1];
+                    const float4 J2 = sh.sj[wib][k][jb][2];
+                    const f32x2 xj = pk(J0.x, J0.y), yj = pk(J0.z, J0.w), zj = pk(J1.x, J1.y);
+                    const f32x2 qj = pk(J1.z, J1.w), sgj = pk(J2.x, J2.y), ej = pk(J2.z, J2.w);
+                    const f32x2 dx = sub2(pk(I0.x, I0.y), xj);
+                    const f32x2 dy = sub2(pk(I0.z, I0.w), yj);
+                    const f32x2 dz = sub2(pk(I1.x, I1.y), zj);
+                    const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+                    const float2 r2s = upk(r2);
+                    if (PRUNE) {
+                        kb |= (((lb >> (2 * p)) & 1u) && r2s.x < rp2) ? 1u << (2 * p) : 0u;
+                        kb |= (((lb >> (2 * p + 1)) & 1u) && r2s.y < rp2) ? 2u << (2 * p) : 0u;
+                    }
+                    const bool ina = ((lb >> (2 * p)) & 1u) && (r2s.x < rc2);
+                    const bool inb = ((lb >> (2 * p + 1)) & 1u) && (r2s.y < rc2);
+                    const f32x2 rinv = pk(rsqrtf(r2s.x), rsqrtf(r2s.y));
+                    const f32x2 r2inv = mul2(rinv, rinv);
+                    const f32x2 sg = add2(pk(I2.x, I2.y), sgj);
+                    const f32x2 sr2 = mul2(mul2(sg, sg), r2inv);
+                    const f32x2 sr6 = mul2(mul2(sr2, sr2), sr2);
+                    const f32x2 e4s6 = mul2(mul2(pk(I2.z, I2.w), ej), sr6);
+                    const f32x2 qq = mul2(pk(I1.z, I1.w), qj);
+                    const float2 s6 = upk(sr6);  // 12 s^6 - 6 with immediate operands
+                    const f32x2 t = pk(fmaf(12.f, s6.x, -6.f), fmaf(12.f, s6.y, -6.f));
+                    const f32x2 b = fma2(qq, rinv, mul2(e4s6, t));
+                    float2 f = upk(fma2(b, r2inv, mul2(qq, nkrf2)));
+                    f.x = ina ? f.x : 0.f;
+                    f.y = inb ? f.y : 0.f;
+                    const f32x2 fs = pk(f.x, f.y);
+                    fi[p][0] = fma2(fs, dx, fi[p][0]);
+                    fi[p][1] = fma2(fs, dy, fi[p][1]);
+                    fi[p][2] = fma2(fs, dz, fi[p][2]);
+                    fjx = fma2(fs, dx, fjx);
+                    fjy = fma2(fs, dy, fjy);
+                    fjz = fma2(fs, dz, fjz);
+                }
+            }
+            if (PRUNE) {
+                const unsigned keep = __reduce_or_sync(FULL, kb);
+                keep_l = lane == k ? keep : keep_l;
+            }
+            const float2 jx = upk(fjx), jy = upk(fjy), jz = upk(fjz);
+            flush_j(d, gj, ia, jx.x + jx.y, jy.x + jy.y, jz.x + jz.y);
+        };
+        int k = 0;
+        for (; k + 1 < ne; k += 2) {
+            entry(k);
+            entry(k + 1);
+        }
+        if (k < ne) entry(k);
+        // flush the i-forces at the same 32-entry boundaries as the scalar variants
+        if (((eb - it.y) & 31) == 32 - EPC2 || eb + EPC2 >= it.z) {
+            float fs[NIC][3];
+#pragma unroll
+            for (int p = 0; p < NIC / 2; ++p) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float2 t = upk(fi[p][c]);
+                    fs[2 * p][c] = t.x;
+                    fs[2 * p + 1][c] = t.y;
+                    fi[p][c] = 0ull;
+                }
+            }
+            flush_i(d, gS, ia, jb, touched, fs);
+            touched = 0;
+        }
+        if (PRUNE && lane < ne) d.ent_hdr[ebase + eb + lane].y = (hy_l & ~0xff00) | (int)(keep_l << 8);
+    }
+}
+
+template <int WARPS>
+__device__ __noinline__ void item_entries_x2_prune(const Dev &d, PairShared2<WARPS> &sh, const SysDev &S, int4 it,
+                                                   int gS) {
+    item_entries_x2<WARPS, 8, true>(d, sh, S, it, gS);
+}
+
 template <int WARPS, int MSHIFT>
 __device__ __forceinline__ void normal_items_x2(const Dev &d, int w0, int w1, int nblk, PairShared2<WARPS> &sh) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int ia = lane & 7, jb = lane >> 3;
     const int nw = w1 - w0;
     const int total = sh.pre[nw];
     for (;;) {
@@ -332,113 +498,8 @@ __device__ __forceinline__ void normal_items_x2(const Dev &d, int w0, int w1, in
             f[8 + h] = l.x;
             f[10 + h] = l.y;
         }
-        const float L = S.boxf, rc2 = S.rc2;
-        const f32x2 nkrf2 = pk(-2.0f * S.krf, -2.0f * S.krf);
-        f32x2 fi[NIC / 2][3];
-#pragma unroll
-        for (int p = 0; p < NIC / 2; ++p) fi[p][0] = fi[p][1] = fi[p][2] = 0ull;
-        unsigned touched = 0;
-        const size_t ebase = (size_t)sc * d.ent_cap;
-        for (int eb = it.y; eb < it.z; eb += EPC2) {
-            const int ne = min(EPC2, it.z - eb);
-            int gj_l = 0;
-            unsigned im_l = 0;
-            __syncwarp();
-            if (lane < ne) {
-                const int2 hdr = d.ent_hdr[ebase + eb + lane];
-                gj_l = hdr.x;
-                im_l = ((unsigned)hdr.y >> MSHIFT) & 0xffu;
-                const float sx = (float)((hdr.y & 3) - 1) * L;
-                const float sy = (float)(((hdr.y >> 2) & 3) - 1) * L;
-                const float sz = (float)(((hdr.y >> 4) & 3) - 1) * L;
-#pragma unroll
-                for (int q = 0; q < JC; ++q) {
-                    float4 x = d.xq[gj_l + q];
-                    const float2 l = d.lj[gj_l + q];
-                    x.x += sx;
-                    x.y += sy;
-                    x.z += sz;
-                    sh.sj[wib][lane][q][0] = make_float4(x.x, x.x, x.y, x.y);
-                    sh.sj[wib][lane][q][1] = make_float4(x.z, x.z, x.w, x.w);
-                    sh.sj[wib][lane][q][2] = make_float4(l.x, l.x, l.y, l.y);
-                }
-                const uint4 *src = reinterpret_cast<const uint4 *>(d.ent_lb + 32 * (ebase + eb + lane));
-                uint4 *dst = reinterpret_cast<uint4 *>(&sh.lb[wib][lane][0]);
-                dst[0] = src[0];
-                dst[1] = src[1];
-            }
-            __syncwarp();
-            auto entry = [&](int k) {
-                const unsigned imask = __shfl_sync(FULL, im_l, k);
-                const int gj = __shfl_sync(FULL, gj_l, k) + jb;
-                const unsigned lb = sh.lb[wib][k][lane];
-                touched |= imask;
-                f32x2 fjx = 0ull, fjy = 0ull, fjz = 0ull;  // (even, odd) i-clusters
-#pragma unroll
-                for (int p = 0; p < NIC / 2; ++p) {
-                    if (imask & (3u << (2 * p))) {
-                        const float4 I0 = sh.si[wib][p][ia][0], I1 = sh.si[wib][p][ia][1];
-                        const float4 I2 = sh.si[wib][p][ia][2];
-                        // j operands re-read per i-cluster pair: keeps 12 registers free
-                        const float4 J0 = sh.sj[wib][k][jb][0], J1 = sh.sj[wib][k][jb][1];
-                        const float4 J2 = sh.sj[wib][k][jb][2];
-                        const f32x2 xj = pk(J0.x, J0.y), yj = pk(J0.z, J0.w), zj = pk(J1.x, J1.y);
-                        const f32x2 qj = pk(J1.z, J1.w), sgj = pk(J2.x, J2.y), ej = pk(J2.z, J2.w);
-                        const f32x2 dx = sub2(pk(I0.x, I0.y), xj);
-                        const f32x2 dy = sub2(pk(I0.z, I0.w), yj);
-                        const f32x2 dz = sub2(pk(I1.x, I1.y), zj);
-                        const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-                        const float2 r2s = upk(r2);
-                        const bool ina = ((lb >> (2 * p)) & 1u) && (r2s.x < rc2);
-                        const bool inb = ((lb >> (2 * p + 1)) & 1u) && (r2s.y < rc2);
-                        const f32x2 rinv = pk(rsqrtf(r2s.x), rsqrtf(r2s.y));
-                        const f32x2 r2inv = mul2(rinv, rinv);
-                        const f32x2 sg = add2(pk(I2.x, I2.y), sgj);
-                        const f32x2 sr2 = mul2(mul2(sg, sg), r2inv);
-                        const f32x2 sr6 = mul2(mul2(sr2, sr2), sr2);
-                        const f32x2 e4s6 = mul2(mul2(pk(I2.z, I2.w), ej), sr6);
-                        const f32x2 qq = mul2(pk(I1.z, I1.w), qj);
-                        const float2 s6 = upk(sr6);  // 12 s^6 - 6 with immediate operands
-                        const f32x2 t = pk(fmaf(12.f, s6.x, -6.f), fmaf(12.f, s6.y, -6.f));
-                        const f32x2 b = fma2(qq, rinv, mul2(e4s6, t));
-                        float2 f = upk(fma2(b, r2inv, mul2(qq, nkrf2)));
-                        f.x = ina ? f.x : 0.f;
-                        f.y = inb ? f.y : 0.f;
-                        const f32x2 fs = pk(f.x, f.y);
-                        fi[p][0] = fma2(fs, dx, fi[p][0]);
-                        fi[p][1] = fma2(fs, dy, fi[p][1]);
-                        fi[p][2] = fma2(fs, dz, fi[p][2]);
-                        fjx = fma2(fs, dx, fjx);
-                        fjy = fma2(fs, dy, fjy);
-                        fjz = fma2(fs, dz, fjz);
-                    }
-                }
-                const float2 jx = upk(fjx), jy = upk(fjy), jz = upk(fjz);
-                flush_j(d, gj, ia, jx.x + jx.y, jy.x + jy.y, jz.x + jz.y);
-            };
-            int k = 0;
-            for (; k + 1 < ne; k += 2) {
-                entry(k);
-                entry(k + 1);
-            }
-            if (k < ne) entry(k);
-            // flush the i-forces at the same 32-entry boundaries as the scalar variants
-            if (((eb - it.y) & 31) == 32 - EPC2 || eb + EPC2 >= it.z) {
-                float fs[NIC][3];
-#pragma unroll
-                for (int p = 0; p < NIC / 2; ++p) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float2 t = upk(fi[p][c]);
-                        fs[2 * p][c] = t.x;
-                        fs[2 * p + 1][c] = t.y;
-                        fi[p][c] = 0ull;
-                    }
-                }
-                flush_i(d, gS, ia, jb, touched, fs);
-                touched = 0;
-            }
-        }
+        if (MSHIFT == 8 && d.prune_now[w] != 0ull) item_entries_x2_prune<WARPS>(d, sh, S, it, gS);
+        else item_entries_x2<WARPS, MSHIFT, false>(d, sh, S, it, gS);
     }
     if (lane == 0) {
         __threadfence();

@@ -272,6 +272,7 @@ size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io
     d.pending = a.take<int>(L.W);
     d.rebuild = a.take<int>(L.W);
     d.prune = a.take<int>(L.W);
+    d.prune_now = a.take<unsigned long long>(L.W);
     d.eterm = a.take<long long>((size_t)L.W * N_ETERMS);
     d.abf_sum = a.take<double>(L.total_bins);
     d.abf_sumsq = a.take<double>(L.total_bins);
@@ -394,13 +395,14 @@ int sync_status(la_handle *h, cudaStream_t s, unsigned *bits) {
 // launch for pairs, bonded terms, walker terms and the lambda update
 int enqueue_step(la_handle *h, int w0, int w1, cudaStream_t s) {
     launch_integrate(h->d, h->hv, w0, w1, s);
-    launch_rebuild(h->d, h->hv, w0, w1, s);
-    launch_prune(h->d, h->hv, w0, w1, s);
+    launch_gate(h->d, w0, w1, 0, false, s);
+    launch_rebuild(h->d, h->hv, w0, w1, s, true);
     launch_pairs_fused(h->d, h->hv, (int)h->stages.size(), s);
     return 0;
 }
 
-int kernels_per_step(la_handle *h) { return 1 + rebuild_kernel_count(h->hv, 0, h->L.W) + 1 + 1; }
+// integrate, gate, list kernels, fused pair launch
+int kernels_per_step(la_handle *h) { return 1 + 1 + rebuild_kernel_count(h->hv, 0, h->L.W) + 1; }
 
 // evaluate forces, dU/dlambda and G at the current state of walkers [w0, w1)
 int prime(la_handle *h, int w0, int w1, bool force_rebuild, bool energy, cudaStream_t s) {
@@ -457,9 +459,9 @@ int capture_graph(la_handle *h) {
         CU(h, cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, nullptr, nullptr, nullptr));
         cudaGraphConditionalHandle hc;
         CU(h, cudaGraphConditionalHandleCreate(&hc, cg, 0, cudaGraphCondAssignDefault));
-        launch_gate(h->d, 0, W, hc, cs);
+        launch_gate(h->d, 0, W, hc, true, cs);
         CU(h, cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, &deps, nullptr, &nd));
-        // IF (some walker must rebuild or prune) { list kernels, pruning }
+        // IF (some walker must rebuild) { list kernels }
         cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
         p.conditional.handle = hc;
         p.conditional.type = cudaGraphCondTypeIf;
@@ -468,8 +470,7 @@ int capture_graph(la_handle *h) {
         CU(h, cudaGraphAddNode(&prev, cg, deps, nullptr, nd, &p));
         cudaGraph_t body = p.conditional.phGraph_out[0];
         CU(h, cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        launch_rebuild(h->d, h->hv, 0, W, cb);
-        launch_prune(h->d, h->hv, 0, W, cb);
+        launch_rebuild(h->d, h->hv, 0, W, cb, true);
         cudaGraph_t body_out;
         CU(h, cudaStreamEndCapture(cb, &body_out));
         CU(h, cudaStreamUpdateCaptureDependencies(cs, &prev, nullptr, 1, cudaStreamSetCaptureDependencies));
@@ -479,9 +480,9 @@ int capture_graph(la_handle *h) {
     cudaError_t e = cudaGraphInstantiate(&h->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, LA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    // graph steps: integrate, gate, fused pairs; list and prune kernels are
-    // counted per step that runs them (device counter)
-    h->graph_launches_per_step = h->launches_per_step - rebuild_kernel_count(h->hv, 0, W) - 1 + 1;
+    // graph steps: integrate, gate, fused pairs; list kernels are counted per
+    // step that runs them (device counter)
+    h->graph_launches_per_step = h->launches_per_step - rebuild_kernel_count(h->hv, 0, W);
     return LA_OK;
 }
 
@@ -1415,7 +1416,7 @@ int la_stats(la_handle *h, int64_t *out, void *stream) {
         out[0] = h->steps;
         out[1] = (int64_t)c[0];
         // list kernels run inside the graph only on rebuild steps (counted by the gate)
-        out[2] = h->launches + (int64_t)c[6] * (rebuild_kernel_count(h->hv, 0, h->L.W) + 1);
+        out[2] = h->launches + (int64_t)c[6] * rebuild_kernel_count(h->hv, 0, h->L.W);
         out[3] = (int64_t)c[1];
         out[4] = (int64_t)c[2];
         out[5] = ents;
@@ -1432,7 +1433,7 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
     rc = flush_dirty(h, s);
     if (rc != LA_OK) return rc;
     const int W = h->L.W;
-    cudaEvent_t ev[4];  // integrate | list kernels + pruning | fused pair launch
+    cudaEvent_t ev[4];  // integrate | gate + list kernels | fused pair launch
     for (auto &e : ev) CU(h, cudaEventCreate(&e));
     double acc[LA_N_KERNELS] = {0};
     int64_t cnt[LA_N_KERNELS] = {0};
@@ -1440,8 +1441,8 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
         cudaEventRecord(ev[0], s);
         launch_integrate(h->d, h->hv, 0, W, s);
         cudaEventRecord(ev[1], s);
-        launch_rebuild(h->d, h->hv, 0, W, s);
-        launch_prune(h->d, h->hv, 0, W, s);
+        launch_gate(h->d, 0, W, 0, false, s);
+        launch_rebuild(h->d, h->hv, 0, W, s, true);
         cudaEventRecord(ev[2], s);
         // the fused launch of the batched step: pairs, bonded terms, walker
         // terms and the lambda update
@@ -1454,7 +1455,7 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
             acc[q] += ms;
         }
         cnt[0] += 1;
-        cnt[1] += rebuild_kernel_count(h->hv, 0, W) + 1;
+        cnt[1] += 1 + rebuild_kernel_count(h->hv, 0, W);
         cnt[2] += 1;
     }
     launch_finish(h->d, h->hv, 0, W, s);

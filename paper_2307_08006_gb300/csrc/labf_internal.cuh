@@ -165,7 +165,9 @@ struct Dev {
     unsigned int *status;
     unsigned int *wdone, *sdone;  // arrivals per walker / per stage in the fused pair launch
     float4 *xprune;               // positions at the last pruning, per slot
-    int *prune;                   // per walker: prune the tiles before the next fused step
+    int *prune;                   // per walker: pruning requested (displacement or fresh list)
+    unsigned long long *prune_now;  // per walker: 0, or 1 + the step counter of the batched
+                                    // step whose pair pass re-prunes the walker's tiles
     unsigned long long *counters; // [0] rebuilds [1] pairs normal [2] pairs alch [4, 5] pair
                                   // work items [6] rebuild events [8, 9] list-build work items
 };

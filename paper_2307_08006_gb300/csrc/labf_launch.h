@@ -21,10 +21,12 @@ struct HostView {
 
 void launch_integrate(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
 void launch_finish(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
-void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
+// batched: the batched step's chain (fresh lists are pruned by its pair pass)
+void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s, bool batched = false);
 void launch_items(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
-void launch_gate(const Dev &d, int w0, int w1, cudaGraphConditionalHandle handle, cudaStream_t s);
-void launch_prune(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s);
+// conditional: also set the graph's conditional handle (false outside graphs)
+void launch_gate(const Dev &d, int w0, int w1, cudaGraphConditionalHandle handle, bool conditional,
+                 cudaStream_t s);
 int rebuild_kernel_count(const HostView &hv, int w0, int w1);
 void launch_pairs(const Dev &d, const HostView &hv, int w0, int w1, bool energy, cudaStream_t s);
 // pairs + bonded + walker terms + lambda update of all walkers in one launch

@@ -240,14 +240,18 @@ def test_pair_kernel_launch_shapes_bit_identical():
         make_engine(sp, run, state=st, chunk_entries=48)
 
 
-def test_dynamic_pruning_skips_tiles_without_changing_results():
-    """The batched step skips tiles with no listed pair within r_c + margin
-    (re-pruned whenever an atom moved 0.45 margin): fewer tiles, the same
-    bits as without pruning and as the one-walker-per-launch form."""
+@pytest.mark.parametrize("variant", range(6))
+def test_dynamic_pruning_skips_tiles_without_changing_results(variant):
+    """The batched step's pair pass re-prunes a walker's tiles (keeping those
+    with a listed pair within r_c + margin) whenever one of its atoms moved
+    0.45 margin, and skips the pruned tiles until then: fewer tiles, the same
+    bits as without pruning and as the one-walker-per-launch form, for every
+    kernel variant."""
     sp = small_water(n_w=137, n_s=5, box=1.7, seed=5, jitter=0.03)
     run = synth.water_run(walkers_per_stage=2, n_bins=20, skin=0.15)
     st = synth.initial_state(sp, run, lam0=[0.1, 0.3, 0.6, 0.8])
-    eng = {m: make_engine(sp, run, state=st, graph_steps=8, prune_margin=m)[0] for m in (0.0, 0.05, 0.1)}
+    eng = {m: make_engine(sp, run, state=st, graph_steps=8, prune_margin=m, pair_variant=variant)[0]
+           for m in (0.0, 0.05, 0.1)}
     plain, _ = make_engine(sp, run, state=st, graph_steps=8)
     for e in eng.values():
         e.step(57)
@@ -260,6 +264,36 @@ def test_dynamic_pruning_skips_tiles_without_changing_results():
             a = e.get_state(w)
             assert np.array_equal(a["x"], ref["x"]) and np.array_equal(a["v"], ref["v"])
             assert a["lam"] == ref["lam"] and a["plam"] == ref["plam"]
+
+
+def test_dynamic_pruning_across_forms_and_state_changes():
+    """Pruned masks stay valid when the batched step alternates with the
+    one-walker-per-launch form, the no-graph form and the kernel timer, and
+    when a walker's state is replaced: bit-identical to an engine without
+    pruning driven the same way."""
+    sp = small_water(n_w=137, n_s=5, box=1.7, seed=9, jitter=0.03)
+    run = synth.water_run(walkers_per_stage=2, n_bins=20, skin=0.15)
+    st = synth.initial_state(sp, run, lam0=[0.05, 0.35, 0.55, 0.9])
+    a, _ = make_engine(sp, run, state=st, graph_steps=6, prune_margin=0.04)
+    b, _ = make_engine(sp, run, state=st, graph_steps=6)
+    c, _ = make_engine(sp, run, state=st, graph_steps=-1, prune_margin=0.04)
+    for e in (a, b, c):
+        e.step(23)
+        e.step_plain(5)
+        e.step(17)
+        e.time_kernels(4)
+        e.step(9)
+    s2 = b.get_state(2)
+    for e in (a, b, c):
+        e.set_state(2, x=s2["x"] + np.float32(0.002), v=s2["v"])
+        e.step(31)
+    for w in range(run.n_walkers):
+        ref = b.get_state(w)
+        for e in (a, c):
+            g = e.get_state(w)
+            assert np.array_equal(g["x"], ref["x"]) and np.array_equal(g["v"], ref["v"])
+            assert g["lam"] == ref["lam"] and g["plam"] == ref["plam"]
+    assert int(a.stats()[6]) < int(b.stats()[6])
 
 
 def test_autotune_leaves_the_trajectory_unchanged():
