@@ -353,7 +353,10 @@ def gpu_arm(args):
     # v (16), x (16), reference x (16), slot indices (8) read; x, v (32) and
     # the cleared F (24) written
     hbm_peak, hbm_src = measured_hbm()
-    integ_bytes = 144.0 * run.n_walkers * spec.n
+    # 88 B read + 56 B written per atom, plus the 16 B reference position
+    # read when pruning is on
+    integ_per_atom = 144.0 + (16.0 if args.prune_margin > 0 else 0.0)
+    integ_bytes = integ_per_atom * run.n_walkers * spec.n
     integ_gbs = integ_bytes / (kt["integrate"][0] * 1e-3) / 1e9
 
     m = re.search(r"pair_variant=(\d+)", eng.autotune_report())
