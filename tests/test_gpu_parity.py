@@ -7,6 +7,8 @@ lambda path exact; short trajectories (same Philox streams) within FP32
 rounding growth; batched and one-walker-per-launch forms bit-identical;
 repeated runs bit-identical.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -86,6 +88,45 @@ def test_pair_set_bit_exact(case):
         assert len(pairs) == len(opairs)
         assert np.array_equal(pairs, opairs)
         assert np.array_equal(kind, okind)
+
+
+def tie_system():
+    """Atom pairs placed on the quantization grid of a 1 nm box at D == R
+    (not listed), D == R - 1 (listed) and D == R + 1, along the axes and on
+    diagonals (600-800-1000 and 480-600-640-1000 triples), some across the
+    periodic boundary; R = 10^12 (r_list = 10^6 grid units)."""
+    d = 1_000_000
+    offs = [(d, 0, 0), (d - 1, 0, 0), (d + 1, 0, 0), (0, -d, 0), (0, -(d - 1), 0), (0, 0, d),
+            (0, 0, -(d - 1)), (600000, 800000, 0), (600000, 799999, 0), (600000, 800001, 0),
+            (-800000, 0, 600000), (-799999, 0, 600000), (480000, 600000, 640000),
+            (480000, 600000, 639999), (-480000, -600000, 640001), (480000, -599999, -640000)]
+    g, U = 4194304, 2 ** 24  # groups a quarter box apart; bases near the upper edge wrap
+    u = []
+    for k in range(64):
+        b = np.array([(k % 4) * g + U - 300000, ((k // 4) % 4) * g + U - 300000, (k // 16) * g + 150000])
+        u.append(b % U)
+        u.append((b + np.array(offs[k % 16])) % U)
+    u = np.array(u, np.int64)
+    n = len(u)
+    x = (u * 2.0 ** -24).astype(np.float32)  # exact: 24 significant bits at most
+    sp = synth.SystemSpec(name="ties", box=1.0, mass=np.ones(n), charge=np.zeros(n),
+                          sigma=np.full(n, 0.001), epsilon=np.zeros(n), alch=np.zeros(n, np.uint8),
+                          excl_group=np.full(n, -1, np.int32), excl_extra=np.full((n, 4), -1, np.int32),
+                          x=x, r_cut=800000 * 2.0 ** -24)
+    run = dataclasses.replace(synth.lj_fluid_run(n_walkers=1), skin=200000 * 2.0 ** -24)
+    expect = sum(1 for k in range(64) if sum(c * c for c in offs[k % 16]) < d * d)
+    return sp, run, expect
+
+
+def test_pair_set_exact_ties():
+    sp, run, expect = tie_system()
+    osys = oracle.OracleSystem(sp)
+    opairs, okind = oracle.pair_set(osys, sp.x, sp.r_cut + run.skin)
+    assert len(opairs) == expect == 28
+    eng, st = make_engine(sp, run)
+    pairs, kind = eng.get_pairs(0)
+    assert np.array_equal(pairs, opairs)
+    assert np.array_equal(kind, okind)
 
 
 @pytest.mark.parametrize("lam0", [[0.0, 0.13, 0.37, 0.5], [0.5, 0.62, 0.91, 1.0]])
