@@ -493,6 +493,28 @@ def test_harmonic_switch_free_energy_closed_form():
 
 
 @pytest.mark.slow
+def test_delta_a_does_not_depend_on_the_bias_ramp():
+    """The bias depends on lambda only, so it changes where the walkers go but
+    not the conditional mean of dU/dlambda in a bin (Sec. 2.3): Delta A is the
+    same closed form for a ramp that reaches full bias after 10 samples and
+    one that needs 10^5 (about 8000 samples per bin here: the bias stays
+    below a tenth of the mean force for the whole run)."""
+    out = {}
+    for n_full in (10.0, 1e5):
+        vals = []
+        for seed in range(3):
+            sp = synth.harmonic_well(dims=1, k0=1.0, k1=4.0)
+            run = synth.harmonic_run(seed=500 + seed, n_walkers=4, n_full=n_full)
+            sim = oracle.Simulation(sp, run)
+            sim.run(100_000)
+            vals.append(sim.delta_a(0)[2])
+        out[n_full] = np.mean(vals)
+    for v in out.values():
+        assert v == pytest.approx(0.5 * np.log(4.0), abs=0.05)
+    assert abs(out[10.0] - out[1e5]) < 0.05
+
+
+@pytest.mark.slow
 def test_fixed_lambda_windows_closed_form():
     """Fixed-lambda windows (the comparison method of Sec. 4): each window's
     mean <dU/dlambda> is the closed form (d kT/2)(k1 - k0)/k(lambda_c) and the
