@@ -430,7 +430,7 @@ def main():
     ap.add_argument("--skin", type=float, default=SKIN_NM, help="list skin (nm)")
     ap.add_argument("--prune-margin", type=float, default=PRUNE_NM,
                     help="pair-pass pruning margin (nm); 0 = off")
-    ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
+    ap.add_argument("--out-dir", default=os.path.join(ROOT, "bench_out"), help="clock samples (CSV)")
     args = ap.parse_args()
     os.makedirs(args.out_dir, exist_ok=True)
     if args.impl == "reference":

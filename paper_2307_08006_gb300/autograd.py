@@ -8,7 +8,8 @@ storage) and evaluates U; the same engine call also returns -dU/dx (forces),
 dU/dlambda and dU/dtheta, which backward() scales by the incoming gradient.
 The arithmetic is entirely in the CUDA library; this module only moves
 tensors.  The paper does not differentiate with respect to force-field
-parameters; this is the north-star's differentiation pattern.
+parameters; gradients of U and of Delta A with respect to the solute's
+parameters are an extension of this library.
 """
 from __future__ import annotations
 
