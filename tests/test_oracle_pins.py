@@ -131,6 +131,73 @@ def test_softcore_finite_at_overlap(n, m):
         assert res["terms"][2] == pytest.approx(lv ** n * 4 * (1 / s ** 2 - 1 / s), rel=1e-6)
 
 
+def _bare(n, x, box=3.0, mass=None, group=None, **kw):
+    """n uncharged atoms with no Lennard-Jones interaction."""
+    return synth.SystemSpec(
+        name="bare", box=box, mass=np.ones(n) if mass is None else np.asarray(mass, float),
+        charge=np.zeros(n), sigma=np.zeros(n), epsilon=np.zeros(n), alch=np.zeros(n, np.uint8),
+        excl_group=np.full(n, -1, np.int32) if group is None else np.asarray(group, np.int32),
+        excl_extra=np.full((n, 4), -1, np.int32), x=np.asarray(x, np.float32), **kw)
+
+
+@pytest.mark.parametrize("origin", [(1.5, 1.5, 1.5), (2.97, 0.02, 1.0)])
+def test_bonded_terms_closed_form(origin):
+    """A water built with O-H lengths r0 + 0.004 and r0 - 0.003 and an
+    H-O-H angle theta0 + 0.05 rad (second case: the molecule straddles two
+    box faces): U_bond = 1/2 k_b (0.004^2 + 0.003^2), U_angle = 1/2 k_t 0.05^2."""
+    L, r0, t0, kb, kt = 3.0, 0.09572, np.deg2rad(104.52), 502416.0, 628.02
+    o = np.array(origin)
+    th = t0 + 0.05
+    x = np.array([o, o + (r0 + 0.004) * np.array([1.0, 0.0, 0.0]),
+                  o + (r0 - 0.003) * np.array([np.cos(th), -np.sin(th), 0.0])]) % L
+    sp = _bare(3, x, box=L, group=[0, 0, 0], bond_ij=np.array([[0, 1], [0, 2]], np.int32),
+               bond_r0=np.full(2, r0), bond_k=np.full(2, kb), angle_ijk=np.array([[1, 0, 2]], np.int32),
+               angle_t0=np.array([t0]), angle_k=np.array([kt]))
+    res = oracle.energy_forces(oracle.OracleSystem(sp), x, 1.0)
+    assert res["terms"][4] == pytest.approx(0.5 * kb * (0.004 ** 2 + 0.003 ** 2), rel=1e-9)
+    assert res["terms"][5] == pytest.approx(0.5 * kt * 0.05 ** 2, rel=1e-9)
+    assert np.all(res["terms"][[0, 1, 2, 3, 6]] == 0.0)
+    np.testing.assert_allclose(res["F"].sum(axis=0), 0.0, atol=1e-7)  # internal forces
+
+
+def test_restraint_terms_closed_form():
+    """Positional restraint across a box face, flat-bottom restraint on two
+    centres of mass (outside and inside d0) and the lambda-switched well with
+    its dU/dlambda, each against its closed form."""
+    L = 3.0
+    # positional: displacement (0.03, -0.04, 0.012) from a reference just
+    # inside the upper face, the atom wrapped to the lower side
+    x0 = np.array([[2.99, 1.0, 0.005]])
+    x = (x0 + [0.03, -0.04, 0.012]) % L
+    sp = _bare(1, x, box=L, posres_idx=np.array([0], np.int32), posres_x0=x0, posres_k=1000.0)
+    res = oracle.energy_forces(oracle.OracleSystem(sp), x, 0.3)
+    assert res["terms"][6] == pytest.approx(500.0 * (0.03 ** 2 + 0.04 ** 2 + 0.012 ** 2), rel=1e-9)
+    np.testing.assert_allclose(res["F"][0], [-30.0, 40.0, -12.0], rtol=1e-9)
+    # flat bottom: group A = masses 1 and 3 (centre a quarter of the way from
+    # atom 0 to atom 1), group B = one atom; centre distance d0 + 0.02 / d0 - 0.02
+    d0, k = 1.0, 800.0
+    for ex, expect in ((0.02, 0.5 * k * 0.02 ** 2), (-0.02, 0.0)):
+        a0 = np.array([0.5, 1.0, 1.0])
+        a1 = a0 + [0.4, 0.0, 0.0]
+        com = a0 + 0.75 * (a1 - a0)
+        b = com + (d0 + ex) * np.array([0.0, 0.6, 0.8])
+        x = np.array([a0, a1, b])
+        sp = _bare(3, x, box=L, mass=[1.0, 3.0, 2.0], fb_a=np.array([0, 1], np.int32),
+                   fb_b=np.array([2], np.int32), fb_d0=d0, fb_k=k)
+        res = oracle.energy_forces(oracle.OracleSystem(sp), x, 0.5)
+        assert res["terms"][6] == pytest.approx(expect, rel=1e-9, abs=1e-15)
+        np.testing.assert_allclose(res["F"].sum(axis=0), 0.0, atol=1e-9)
+    # lambda-switched well: U = 1/2 ((1 - lambda) k0 + lambda k1) r^2 with r^2 = 0.09
+    x0 = np.array([[1.0, 1.0, 1.0]])
+    x = x0 + [0.1, 0.2, -0.2]
+    sp = _bare(1, x, box=L, lh_idx=np.array([0], np.int32), lh_x0=x0, lh_k0=100.0, lh_k1=400.0, lh_dims=3)
+    for lam in (0.0, 0.25, 1.0):
+        res = oracle.energy_forces(oracle.OracleSystem(sp), x, lam)
+        kl = (1 - lam) * 100.0 + lam * 400.0
+        assert res["terms"][6] == pytest.approx(0.5 * kl * 0.09, rel=1e-9)
+        assert res["dUdl"] == pytest.approx(0.5 * 300.0 * 0.09, rel=1e-9)
+
+
 def test_reaction_field_closed_forms():
     rc = 1.2
     # U(r_c) = 0 for any eps_rf
