@@ -222,6 +222,24 @@ def test_reaction_field_closed_forms():
         assert res["F"][1, 0] == pytest.approx(138.935458 * 0.5 * -0.7 / r ** 2, rel=1e-12)
 
 
+@pytest.mark.parametrize("lam", [0.55, 0.8, 1.0])
+def test_alchemical_rf_scales_linearly(lam):
+    """A pair with one alchemical atom carries lambda_e times the
+    reaction-field energy of the same pair as a normal pair (Sec. 3.1.2), and
+    its dU/dlambda is dlambda_e/dlambda = 1/(1 - b_e) times that energy."""
+    for r in (0.3, 0.7, 1.1):
+        kw = dict(q=(0.5, -0.7), sig=(0.0, 0.0), eps=(0.0, 0.0), rc=1.2, bv=0.5, be=0.5)
+        alch = oracle.energy_forces(oracle.OracleSystem(_two_atoms(r, alch=(1, 0), **kw)),
+                                    _two_atoms(r, **kw).x.astype(np.float64), lam)
+        norm = oracle.energy_forces(oracle.OracleSystem(_two_atoms(r, **kw)),
+                                    _two_atoms(r, **kw).x.astype(np.float64), lam)
+        le = (lam - 0.5) / 0.5
+        assert norm["terms"][1] != 0.0
+        assert alch["terms"][3] == pytest.approx(le * norm["terms"][1], rel=1e-12)
+        assert alch["dUdl"] == pytest.approx(2.0 * norm["terms"][1], rel=1e-12)
+        np.testing.assert_allclose(alch["F"], le * norm["F"], rtol=1e-12)
+
+
 def test_cutoff_truncates():
     sp = _two_atoms(2.6, rc=2.5)
     res = oracle.energy_forces(oracle.OracleSystem(sp), sp.x.astype(np.float64), 1.0)
