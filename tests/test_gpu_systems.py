@@ -83,6 +83,22 @@ def test_uneven_batch_forces_pairs_and_forms():
         assert np.array_equal(a["x"], b["x"]) and a["lam"] == b["lam"]
 
 
+def test_uneven_batch_pruning_bit_identical():
+    """Pruning in the batched pair pass on eight systems of different sizes
+    and cutoffs (each with its own margin threshold and re-pruning trigger):
+    the same bits as the unpruned one-walker-per-launch form."""
+    inputs = _uneven_inputs()
+    a = labf.Engine(inputs, options=dict(prune_margin=0.05))
+    b = labf.Engine(inputs)
+    a.step(40)
+    b.step_plain(40)
+    for ww in (0, 9, 17, 31, 40, 63):
+        ga, gb = a.get_state(ww), b.get_state(ww)
+        assert np.array_equal(ga["x"], gb["x"]) and np.array_equal(ga["v"], gb["v"])
+        assert ga["lam"] == gb["lam"] and ga["plam"] == gb["plam"]
+    assert int(a.stats()[6]) < int(b.stats()[6])
+
+
 # ---------------------------------------------------------------------------
 # differentiation: U(x, lambda, theta) through torch.autograd at 21 lambdas
 # ---------------------------------------------------------------------------
