@@ -799,7 +799,7 @@ void launch_rebuild(const Dev &d, const HostView &hv, int w0, int w1, cudaStream
     k_items<<<nw, 256, 0, s>>>(d, w0, batched ? 1 : 0);
 }
 
-void launch_items(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s) {
+void launch_items(const Dev &d, const HostView &, int w0, int w1, cudaStream_t s) {
     k_items<<<w1 - w0, 256, 0, s>>>(d, w0, 0);
 }
 
