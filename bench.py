@@ -288,30 +288,24 @@ def gpu_arm(args):
 
     # ---- end to end through the C ABI with host buffers ----
     n, W = spec.n, run.n_walkers
-    pin_x = [torch.empty((n, 3), dtype=torch.float32, pin_memory=True) for _ in range(W)]
-    pin_v = [torch.empty((n, 3), dtype=torch.float32, pin_memory=True) for _ in range(W)]
-    host = [eng.get_state(w) for w in range(W)]
-    for w in range(W):
-        pin_x[w].numpy()[:] = host[w]["x"]
-        pin_v[w].numpy()[:] = host[w]["v"]
-    lam = [h["lam"] for h in host]
-    plam = [h["plam"] for h in host]
+    # every walker's state in page-locked buffers, moved with one call each way
+    pin_x = torch.empty((W * n, 3), dtype=torch.float32, pin_memory=True)
+    pin_v = torch.empty((W * n, 3), dtype=torch.float32, pin_memory=True)
+    px, pv = pin_x.numpy(), pin_v.numpy()
+    host = eng.get_states(x=px, v=pv)
+    lam, plam = host["lam"].copy(), host["plam"].copy()
     h2d = W * (2 * n * 3 * 4 + 16)
     d2h_state = W * (2 * n * 3 * 4 + 16)
     nb = sum(s.n_bins for s in run.stages)
     d2h = d2h_state + nb * (8 + 8 + 8)
 
     def e2e_step():
-        for w in range(W):
-            eng.set_state(w, x=pin_x[w].numpy(), v=pin_v[w].numpy(), lam=lam[w], plam=plam[w])
+        eng.set_states(x=px, v=pv, lam=lam, plam=plam)
         eng.step(md, stream)
         for k in range(len(run.stages)):
             eng.read_abf(0, k)
-        for w in range(W):
-            st = eng.get_state(w)
-            pin_x[w].numpy()[:] = st["x"]
-            pin_v[w].numpy()[:] = st["v"]
-            lam[w], plam[w] = st["lam"], st["plam"]
+        st = eng.get_states(x=px, v=pv)
+        lam[:], plam[:] = st["lam"], st["plam"]
 
     e2e_steps = max(2, min(args.steps, 5))
     e2e_step()
@@ -384,7 +378,7 @@ def gpu_arm(args):
             plain_form=dict(value=plain_val, unit=UNIT, md_steps=plain_md,
                             note="one walker per launch sequence, no CUDA graph"),
             e2e=dict(value=e2e_val, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
-                     note="state upload (la_set_state) + la_step_walkers + la_read_abf + la_get_state, "
+                     note="state upload (la_set_states) + la_step_walkers + la_read_abf + la_get_states, "
                           "host<->device copies in the timed region"),
             gpu_launches=launches,
             roofline=dict(bound="alu", achieved=achieved, peak=peak_tflops, unit="TFLOP/s",

@@ -275,6 +275,21 @@ int la_set_state(la_handle *h, int walker, const float *x, const float *v, const
                  const double *plam, void *stream);
 
 /*
+ * la_get_states / la_set_states: the same for every walker at once, with one
+ * synchronisation per call.  x and v (host float32) hold the walkers one
+ * after another in handle order, walker w's [n_atoms][3] block starting at
+ * 3 * (sum of n_atoms over walkers < w); lam and plam (host double) hold one
+ * value per walker; any pointer may be NULL (left unchanged / not read).
+ * Page-locked buffers are copied by DMA, others through the driver's
+ * staging.  After la_set_states every walker's lists and forces are
+ * refreshed before the next call that needs them, as after la_set_state.
+ * Synchronising.
+ */
+int la_get_states(la_handle *h, float *x, float *v, double *lam, double *plam, void *stream);
+int la_set_states(la_handle *h, const float *x, const float *v, const double *lam, const double *plam,
+                  void *stream);
+
+/*
  * la_set_alch_params: replace (epsilon, sigma, charge) of the alchemical
  * atoms of system `sys` (host [n_alch][3] double, alchemical atoms in index
  * order) for the differentiation path; forces are re-evaluated.

@@ -1154,6 +1154,56 @@ int la_set_state(la_handle *h, int walker, const float *x, const float *v, const
     return sync_status(h, s, nullptr);
 }
 
+int la_get_states(la_handle *h, float *x, float *v, double *lam, double *plam, void *stream) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int W = h->L.W;
+    float *io = (float *)h->io;
+    size_t off = 0;  // float offset of walker w's block in x and v
+    for (int w = 0; w < W; ++w) {
+        const int n = h->sys[h->walk[w].sys].n_atoms;
+        if (x || v) {
+            // the staging area is reused walker after walker: stream order puts
+            // each copy-out before the next walker's gather
+            launch_state_io(h->d, w, n, io, io + 3 * (size_t)n, false, s);
+            if (x) CU(h, cudaMemcpyAsync(x + off, io, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+            if (v) CU(h, cudaMemcpyAsync(v + off, io + 3 * (size_t)n, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+        }
+        off += 3 * (size_t)n;
+    }
+    if (lam) CU(h, cudaMemcpyAsync(lam, h->d.lam, sizeof(double) * W, cudaMemcpyDeviceToHost, s));
+    if (plam) CU(h, cudaMemcpyAsync(plam, h->d.plam, sizeof(double) * W, cudaMemcpyDeviceToHost, s));
+    CU(h, cudaStreamSynchronize(s));
+    return LA_OK;
+}
+
+int la_set_states(la_handle *h, const float *x, const float *v, const double *lam, const double *plam,
+                  void *stream) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    if (h->sticky != LA_OK) return fail(h, LA_ERR_STATE, "handle in error state: %s", h->err.c_str());
+    cudaStream_t s = (cudaStream_t)stream;
+    const int W = h->L.W;
+    float *io = (float *)h->io;
+    size_t off = 0;
+    for (int w = 0; w < W; ++w) {
+        const int n = h->sys[h->walk[w].sys].n_atoms;
+        if (x || v) {
+            // read back the current state first when one of the two stays unchanged
+            if (!x || !v) launch_state_io(h->d, w, n, io, io + 3 * (size_t)n, false, s);
+            if (x) CU(h, cudaMemcpyAsync(io, x + off, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+            if (v) CU(h, cudaMemcpyAsync(io + 3 * (size_t)n, v + off, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+            launch_state_io(h->d, w, n, io, io + 3 * (size_t)n, true, s);
+        }
+        off += 3 * (size_t)n;
+    }
+    if (lam) CU(h, cudaMemcpyAsync(h->d.lam, lam, sizeof(double) * W, cudaMemcpyHostToDevice, s));
+    if (plam) CU(h, cudaMemcpyAsync(h->d.plam, plam, sizeof(double) * W, cudaMemcpyHostToDevice, s));
+    std::vector<int> one(W, 1);
+    CU(h, cudaMemcpyAsync(h->d.rebuild, one.data(), sizeof(int) * W, cudaMemcpyHostToDevice, s));
+    h->dirty = true;
+    return sync_status(h, s, nullptr);  // also keeps `one` alive until the copy is done
+}
+
 int la_set_alch_params(la_handle *h, int sys, const double *theta, void *stream) {
     if (!h || !theta) return LA_ERR_INVALID_ARG;
     if (sys < 0 || sys >= (int)h->sys.size()) return fail(h, LA_ERR_INVALID_ARG, "bad system");

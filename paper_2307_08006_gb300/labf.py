@@ -32,7 +32,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "BOX_TOO_SMALL", -3: "CUDA", -4: "UNSUPPORTED",
           -6: "LIST_OVERFLOW", -7: "NONFINITE", -8: "FIXED_OVERFLOW", -9: "STATE"}
 
 EXPORTED = ("la_query_sizes", "la_create_system", "la_step_walkers", "la_step_walkers_plain",
-            "la_read_abf", "la_abf_export", "la_abf_import", "la_energy_forces", "la_get_state", "la_set_state", "la_set_alch_params",
+            "la_read_abf", "la_abf_export", "la_abf_import", "la_energy_forces", "la_get_state", "la_set_state", "la_get_states", "la_set_states",
+            "la_set_alch_params",
             "la_read_theta", "la_get_pairs", "la_lambda_path", "la_sync", "la_stats",
             "la_time_kernels", "la_autotune", "la_autotune_report", "la_last_error", "la_destroy",
             "la_alch_pairs_static", "la_static_last_error")
@@ -110,6 +111,8 @@ def load(build_if_missing: bool = False):
     lib.la_energy_forces.argtypes = [H, I, C.c_uint32, P, P, P, P, P, P]
     lib.la_get_state.argtypes = [H, I, P, P, P, P, P, P]
     lib.la_set_state.argtypes = [H, I, P, P, P, P, P]
+    lib.la_get_states.argtypes = [H, P, P, P, P, P]
+    lib.la_set_states.argtypes = [H, P, P, P, P, P]
     lib.la_set_alch_params.argtypes = [H, I, P, P]
     lib.la_read_theta.argtypes = [H, I, I, P, P, P, P, P]
     lib.la_get_pairs.argtypes = [H, I, P, P, C.c_int64, P, P]
@@ -252,6 +255,9 @@ class Engine:
                 self.walker_sys.append(si)
                 self.walker_local.append(wl)
         self.n_walkers = len(self.walker_sys)
+        # first row of each walker in the all-walker state arrays
+        sizes = [self.systems[si].spec.n for si in self.walker_sys]
+        self.walker_rows = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
 
     # -- plumbing -------------------------------------------------------
     def _stream(self, stream=None):
@@ -354,6 +360,31 @@ class Engine:
         la = None if lam is None else C.byref(C.c_double(float(lam)))
         pa = None if plam is None else C.byref(C.c_double(float(plam)))
         self._check(self.lib.la_set_state(self.handle, walker, _p(xa), _p(va), la, pa, self._stream(stream)))
+
+    def _rows_array(self, a, name):
+        n = int(self.walker_rows[-1])
+        if a.dtype != np.float32 or a.shape != (n, 3) or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name}: expected a C-contiguous float32 array of shape ({n}, 3)")
+        return a
+
+    def get_states(self, x=None, v=None, stream=None) -> dict:
+        """Every walker's state in one call.  x, v: float32 [rows, 3], walker w
+        in rows walker_rows[w]:walker_rows[w + 1]; pass arrays (e.g. views of
+        page-locked tensors) to have them filled in place."""
+        n = int(self.walker_rows[-1])
+        x = np.zeros((n, 3), np.float32) if x is None else self._rows_array(x, "x")
+        v = np.zeros((n, 3), np.float32) if v is None else self._rows_array(v, "v")
+        lam, plam = np.zeros(self.n_walkers), np.zeros(self.n_walkers)
+        self._check(self.lib.la_get_states(self.handle, _p(x), _p(v), _p(lam), _p(plam), self._stream(stream)))
+        return dict(x=x, v=v, lam=lam, plam=plam)
+
+    def set_states(self, x=None, v=None, lam=None, plam=None, stream=None):
+        """Every walker's state in one call (layout as in get_states)."""
+        xa = None if x is None else self._rows_array(x, "x")
+        va = None if v is None else self._rows_array(v, "v")
+        la = None if lam is None else np.ascontiguousarray(lam, np.float64).reshape(self.n_walkers)
+        pa = None if plam is None else np.ascontiguousarray(plam, np.float64).reshape(self.n_walkers)
+        self._check(self.lib.la_set_states(self.handle, _p(xa), _p(va), _p(la), _p(pa), self._stream(stream)))
 
     def set_alch_params(self, sys: int, theta: np.ndarray, stream=None):
         t = np.ascontiguousarray(theta, np.float64)

@@ -110,3 +110,16 @@ def test_walker_limit():
     sp = synth.lj_fluid()
     assert _query(sp, synth.lj_fluid_run(n_walkers=256))[0] == 0
     assert _query(sp, synth.lj_fluid_run(n_walkers=257))[0] == -1
+
+
+def test_calls_reject_a_null_handle():
+    """Every handle call returns LA_ERR_INVALID_ARG for a NULL handle without
+    touching the device (no GPU needed)."""
+    lib = labf.load()
+    x = np.zeros((4, 3), np.float32)
+    lam = np.zeros(2)
+    assert lib.la_get_states(None, labf._p(x), labf._p(x), labf._p(lam), labf._p(lam), None) == -1
+    assert lib.la_set_states(None, labf._p(x), labf._p(x), labf._p(lam), labf._p(lam), None) == -1
+    assert lib.la_get_state(None, 0, labf._p(x), labf._p(x), None, None, None, None) == -1
+    assert lib.la_set_state(None, 0, labf._p(x), labf._p(x), None, None, None) == -1
+    assert lib.la_step_walkers(None, 1, None) == -1

@@ -83,6 +83,40 @@ def test_uneven_batch_forces_pairs_and_forms():
         assert np.array_equal(a["x"], b["x"]) and a["lam"] == b["lam"]
 
 
+def test_all_walker_state_calls_match_per_walker_calls():
+    """la_get_states / la_set_states over eight systems of different sizes:
+    the same values as the per-walker calls, and the same trajectory after
+    setting every walker either way (also with x alone)."""
+    inputs = _uneven_inputs()
+    eng = labf.Engine(inputs)
+    eng.step(5)
+    st = eng.get_states()
+    rows = eng.walker_rows
+    assert rows[-1] == sum(si.spec.n * si.run.n_walkers for si in inputs)
+    for w in range(eng.n_walkers):
+        g = eng.get_state(w)
+        r0, r1 = rows[w], rows[w + 1]
+        assert np.array_equal(st["x"][r0:r1], g["x"]) and np.array_equal(st["v"][r0:r1], g["v"])
+        assert st["lam"][w] == g["lam"] and st["plam"][w] == g["plam"]
+    x_new = (st["x"] + np.float32(0.001)).astype(np.float32)
+    v_new = (st["v"] * np.float32(0.5)).astype(np.float32)
+    plam_new = -st["plam"]
+    e1, e2 = labf.Engine(inputs), labf.Engine(inputs)
+    e1.set_states(x=x_new, v=v_new, lam=st["lam"], plam=plam_new)
+    for w in range(e2.n_walkers):
+        r0, r1 = rows[w], rows[w + 1]
+        e2.set_state(w, x=x_new[r0:r1], v=v_new[r0:r1], lam=st["lam"][w], plam=plam_new[w])
+    e1.step(7)
+    e2.step(7)
+    a, b = e1.get_states(), e2.get_states()
+    for k in ("x", "v", "lam", "plam"):
+        assert np.array_equal(a[k], b[k]), k
+    # positions alone: velocities stay
+    e1.set_states(x=b["x"])
+    c = e1.get_states()
+    assert np.array_equal(c["x"], b["x"]) and np.array_equal(c["v"], a["v"])
+
+
 def test_uneven_batch_pruning_bit_identical():
     """Pruning in the batched pair pass on eight systems of different sizes
     and cutoffs (each with its own margin threshold and re-pruning trigger):
