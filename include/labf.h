@@ -62,6 +62,7 @@ extern "C" {
 #define LA_STATUS_FIXED_OVERFLOW 0x4u
 #define LA_STATUS_COLUMN_OVERFLOW 0x8u
 #define LA_STATUS_ALCH_OVERFLOW 0x10u
+#define LA_STATUS_BAD_INDEX 0x20u /* la_alch_pairs_static: alch_idx entry not an alchemical atom */
 
 /* ---- energy terms reported by la_energy_forces ---- */
 #define LA_PAIR_VARIANTS 6
@@ -84,9 +85,9 @@ typedef struct la_handle la_handle;
  *   electrostatics coul*q_i*q_j*(1/r + k_rf r^2 - c_rf), both truncated at
  *   r_cut.  A pair with exactly one alchemical atom is scaled: soft-core LJ
  *   lambda_v^sc_n 4 eps (s^-2 - s^-1), s = sc_alpha (1-lambda_v)^sc_m +
- *   (r/sigma)^6, and lambda_e times the RF term.  Pairs of two alchemical
- *   atoms, pairs in the same excl_group (>= 0) and pairs listed in
- *   excl_extra are excluded.  lambda -> (lambda_v, lambda_e) is the
+ *   (r/sigma)^6 (integer powers sc_n, sc_m >= 1), and lambda_e times the
+ *   RF term.  Pairs of two alchemical atoms, pairs in the same excl_group
+ *   (>= 0) and pairs listed in excl_extra are excluded.  lambda -> (lambda_v, lambda_e) is the
  *   piecewise-linear path of Sec. 3.1.1 with breakpoints b_v, b_e.
  *   eps_rf <= 0 selects a conducting continuum.
  *
@@ -410,11 +411,18 @@ int la_destroy(la_handle *h);
  * Inputs (device memory, caller-owned): x [n_atoms][3] float32, q, sigma,
  * epsilon [n_atoms] float32, alch [n_atoms] uint8 (1 = alchemical),
  * excl_group [n_atoms] int32 (-1 = none), alch_idx [n_alch] int32 (the
- * indices of the alchemical atoms, ascending).
+ * indices of the alchemical atoms, ascending, each in [0, n_atoms), flagged
+ * in alch and listed once).  sc_n, sc_m >= 1.
  * Outputs (device memory, caller-owned, overwritten): forces [n_atoms][3]
- * float32 = minus the gradient of these pair terms; out [5] double =
+ * float32 = minus the gradient of these pair terms; out [6] double =
  * {dU/dlambda, dU/dlambda_v, dU/dlambda_e, soft-core LJ energy,
- * lambda_e * RF energy}.
+ * lambda_e * RF energy, status}.  status is 0, or the LA_STATUS_* bits of
+ * what went wrong on the device: LA_STATUS_BAD_INDEX (an alch_idx entry
+ * outside [0, n_atoms) or not flagged alchemical: that atom is skipped),
+ * LA_STATUS_NONFINITE (a non-finite distance or force: the pair is
+ * skipped), LA_STATUS_FIXED_OVERFLOW (a force component of 2^30 or more,
+ * beyond the fixed-point accumulators: skipped).  Any non-zero status
+ * means the other outputs are incomplete.
  *
  * Scratch: one file-scope static device array of 3 * LA_STATIC_MAX_ATOMS
  * 64-bit force accumulators plus 4 * LA_STATIC_MAX_ALCH doubles (about
@@ -429,7 +437,7 @@ int la_destroy(la_handle *h);
  * capture begins.
  *
  * Errors: LA_ERR_INVALID_ARG for NULL pointers, non-positive sizes or box,
- * n_atoms > LA_STATIC_MAX_ATOMS or n_alch > LA_STATIC_MAX_ALCH (the message
+ * sc_n < 1 or sc_m < 1, n_atoms > LA_STATIC_MAX_ATOMS or n_alch > LA_STATIC_MAX_ALCH (the message
  * of la_static_last_error names the limit); LA_ERR_CUDA if the set-up or a
  * launch fails.  Asynchronous on `stream`.
  */

@@ -138,6 +138,11 @@ class OracleSystem:
     arrays alive for the lifetime of the object."""
 
     def __init__(self, spec):
+        # the soft-core derivative carries n lambda_v^(n-1) and
+        # m (1 - lambda_v)^(m-1): integer powers below 1 are not in the
+        # method's family (Beutler form, n, m >= 1) and give 0 * inf at the ends
+        if int(spec.sc_n) < 1 or int(spec.sc_m) < 1:
+            raise ValueError(f"soft-core powers must be >= 1 (sc_n={spec.sc_n}, sc_m={spec.sc_m})")
         self.spec = spec
         keep = {}
 

@@ -4,9 +4,11 @@
 // GPU memory, or a deployment with a fixed device footprint).
 //
 // The scratch holds 64-bit fixed-point force accumulators (so the summed
-// forces do not depend on the order of the atomics) and per-alchemical-atom
-// FP64 partial sums that are folded in a fixed order.  Every call clears the
-// part it uses first.  All calls on a device share the array: calls whose
+// forces do not depend on the order of the atomics), per-alchemical-atom
+// FP64 partial sums that are folded in a fixed order, and one status word
+// (LA_STATUS_* bits: a bad alchemical index, a non-finite distance or force,
+// a force beyond the fixed-point range), reported in out[5].  Every call
+// clears the part it uses first.  All calls on a device share the array: calls whose
 // GPU work overlaps race, so callers must serialise them.
 #include <cuda_runtime.h>
 
@@ -17,14 +19,16 @@
 
 #include "labf_internal.cuh"
 
-// int64 force accumulators, then double partial sums
+// int64 force accumulators, then double partial sums, then the status word
 #define LA_STATIC_FORCE_WORDS (3ull * LA_STATIC_MAX_ATOMS)
 #define LA_STATIC_PART_WORDS (4ull * LA_STATIC_MAX_ALCH)
+#define LA_STATIC_STATUS_WORDS 1ull
 
 // The scratch array (about 3.2 MB on every device that loads the library).
 // Host code must not take its address directly: the name is a host-side
 // stand-in; the device address comes from cudaGetSymbolAddress.
-static __device__ __align__(256) unsigned char g_static_scratch[8 * (LA_STATIC_FORCE_WORDS + LA_STATIC_PART_WORDS)];
+static __device__ __align__(256) unsigned char
+    g_static_scratch[8 * (LA_STATIC_FORCE_WORDS + LA_STATIC_PART_WORDS + LA_STATIC_STATUS_WORDS)];
 
 namespace labf {
 namespace {
@@ -40,20 +44,33 @@ struct StaticParams {
     float le, lvn, dlvn, sa, dsdl;
 };
 
-__global__ void k_static_clear(unsigned long long *F, double *part, int n, int n_alch) {
+__global__ void k_static_clear(unsigned long long *F, double *part, unsigned *status, int n, int n_alch) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += gridDim.x * blockDim.x) F[i] = 0ull;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * n_alch; i += gridDim.x * blockDim.x)
         part[i] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0u;
+}
+
+// a force component that fits the 64-bit fixed-point range, else a status bit
+__device__ __forceinline__ bool static_force_ok(float fx, float fy, float fz, unsigned *status) {
+    const float m = fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz)));
+    if (m < FIX_LIMIT) return true;
+    atomicOr(status, m == m ? LA_STATUS_FIXED_OVERFLOW : LA_STATUS_NONFINITE);
+    return false;
 }
 
 // one warp per alchemical atom; lanes stride over all atoms
 __global__ void k_static_alch(StaticParams p, const float *x, const float *q, const float *sig,
                               const float *eps, const uint8_t *alch, const int *grp, const int *alch_idx,
-                              unsigned long long *F, double *part) {
+                              unsigned long long *F, double *part, unsigned *status) {
     const int lane = threadIdx.x & 31;
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= p.n_alch) return;
     const int a = alch_idx[r];
+    if ((unsigned)a >= (unsigned)p.n || !alch[a]) {  // not an alchemical atom of this system
+        if (lane == 0) atomicOr(status, LA_STATUS_BAD_INDEX);
+        return;
+    }
     const float xa = x[3 * a], ya = x[3 * a + 1], za = x[3 * a + 2];
     const float qa = q[a] * p.sqrt_coul, sa_half = 0.5f * sig[a], ea2 = 2.0f * sqrtf(fmaxf(eps[a], 0.f));
     const int ga = grp[a];
@@ -65,7 +82,10 @@ __global__ void k_static_alch(StaticParams p, const float *x, const float *q, co
         const float dy = min_image(ya - x[3 * b + 1], p.L, p.Linv);
         const float dz = min_image(za - x[3 * b + 2], p.L, p.Linv);
         const float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 >= p.rc2) continue;
+        if (!(r2 < p.rc2)) {
+            if (r2 != r2) atomicOr(status, LA_STATUS_NONFINITE);
+            continue;
+        }
         const float rinv = rsqrtf(r2);
         const float r2inv = rinv * rinv;
         const float qq = qa * q[b] * p.sqrt_coul;
@@ -85,6 +105,7 @@ __global__ void k_static_alch(StaticParams p, const float *x, const float *q, co
             dsc = p.dlvn * e4 * g + p.lvn * e4 * g1 * p.dsdl;
         }
         const float fs = sc_f + p.le * rf_f;
+        if (!static_force_ok(fs * dx, fs * dy, fs * dz, status)) continue;
         fax = fmaf(fs, dx, fax);
         fay = fmaf(fs, dy, fay);
         faz = fmaf(fs, dz, faz);
@@ -104,9 +125,11 @@ __global__ void k_static_alch(StaticParams p, const float *x, const float *q, co
     usc_s = warp_sum(usc_s);
     urf_s = warp_sum(urf_s);
     if (lane == 0) {
-        atomicAdd(F + 3 * (size_t)a, (unsigned long long)__float2ll_rn(fax * F_TO_FIX));
-        atomicAdd(F + 3 * (size_t)a + 1, (unsigned long long)__float2ll_rn(fay * F_TO_FIX));
-        atomicAdd(F + 3 * (size_t)a + 2, (unsigned long long)__float2ll_rn(faz * F_TO_FIX));
+        if (static_force_ok(fax, fay, faz, status)) {
+            atomicAdd(F + 3 * (size_t)a, (unsigned long long)__float2ll_rn(fax * F_TO_FIX));
+            atomicAdd(F + 3 * (size_t)a + 1, (unsigned long long)__float2ll_rn(fay * F_TO_FIX));
+            atomicAdd(F + 3 * (size_t)a + 2, (unsigned long long)__float2ll_rn(faz * F_TO_FIX));
+        }
         part[4 * r] = sv;
         part[4 * r + 1] = se;
         part[4 * r + 2] = usc_s;
@@ -114,9 +137,9 @@ __global__ void k_static_alch(StaticParams p, const float *x, const float *q, co
     }
 }
 
-// forces out in FP32; partial sums folded in alchemical-atom order
-__global__ void k_static_out(const unsigned long long *F, const double *part, int n, int n_alch, double dlv,
-                             double dle, float *forces, double *out) {
+// forces out in FP32; partial sums folded in alchemical-atom order; status
+__global__ void k_static_out(const unsigned long long *F, const double *part, const unsigned *status, int n,
+                             int n_alch, double dlv, double dle, float *forces, double *out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += gridDim.x * blockDim.x)
         forces[i] = fix_to_float(F[i]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -132,6 +155,7 @@ __global__ void k_static_out(const unsigned long long *F, const double *part, in
         out[2] = se;
         out[3] = usc;
         out[4] = urf;
+        out[5] = (double)*status;
     }
 }
 
@@ -182,13 +206,16 @@ extern "C" int la_alch_pairs_static(int n_atoms, const float *x, const float *q,
                  n_atoms, LA_STATIC_MAX_ATOMS, n_alch, LA_STATIC_MAX_ALCH);
         return static_fail(LA_ERR_INVALID_ARG, buf);
     }
-    if (!(box > 0) || !(r_cut > 0) || 2.0 * r_cut > box || !(b_v > 0) || !(b_e < 1) || sc_n < 0 || sc_m < 0)
+    if (!(box > 0) || !(r_cut > 0) || 2.0 * r_cut > box || !(b_v > 0) || !(b_e < 1))
         return static_fail(LA_ERR_INVALID_ARG, "invalid box, cutoff or alchemical parameters");
+    if (sc_n < 1 || sc_m < 1)  // n lambda_v^(n-1) and m (1-lambda_v)^(m-1) at the ends need n, m >= 1
+        return static_fail(LA_ERR_INVALID_ARG, "soft-core powers sc_n and sc_m must be >= 1");
     void *base = nullptr;
     int rc = static_scratch(&base);
     if (rc != LA_OK) return rc;
     unsigned long long *F = (unsigned long long *)base;
     double *part = (double *)(F + LA_STATIC_FORCE_WORDS);
+    unsigned *status = (unsigned *)(part + LA_STATIC_PART_WORDS);
 
     double lv, le, dlv, dle;
     if (lam < b_v) { lv = lam / b_v; dlv = 1.0 / b_v; } else { lv = 1.0; dlv = 0.0; }
@@ -212,10 +239,10 @@ extern "C" int la_alch_pairs_static(int n_atoms, const float *x, const float *q,
 
     cudaStream_t s = (cudaStream_t)stream;
     const int nb = (3 * n_atoms + 255) / 256;
-    k_static_clear<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(F, part, n_atoms, n_alch);
+    k_static_clear<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(F, part, status, n_atoms, n_alch);
     if (n_alch > 0) k_static_alch<<<(n_alch + 3) / 4, 128, 0, s>>>(p, x, q, sigma, epsilon, alch, excl_group,
-                                                                    alch_idx, F, part);
-    k_static_out<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(F, part, n_atoms, n_alch, dlv, dle, forces, out);
+                                                                    alch_idx, F, part, status);
+    k_static_out<<<nb < 1024 ? nb : 1024, 256, 0, s>>>(F, part, status, n_atoms, n_alch, dlv, dle, forces, out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return static_fail(LA_ERR_CUDA, cudaGetErrorString(e));
     return LA_OK;

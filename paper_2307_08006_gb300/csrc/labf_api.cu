@@ -72,8 +72,8 @@ int validate(const la_system_desc *sys, int n_sys, std::string &err) {
         }
         if (!(S.box > 0) || !(S.r_cut > 0) || !(S.skin >= 0) || !(S.dt > 0) || !(S.kT > 0) ||
             !(S.m_lambda > 0) || S.n_stages <= 0 || S.n_stages > 16 || !S.stage_lo || !S.stage_hi ||
-            !S.stage_bins || !S.stage_walkers || !(S.b_v > 0) || !(S.b_e < 1) || S.sc_n < 0 ||
-            S.sc_m < 0 || !(S.n_full > 0) || S.shared_freq < 0) {
+            !S.stage_bins || !S.stage_walkers || !(S.b_v > 0) || !(S.b_e < 1) || S.sc_n < 1 ||
+            S.sc_m < 1 || !(S.n_full > 0) || S.shared_freq < 0) {
             snprintf(buf, sizeof buf, "system %d: invalid parameters", s);
             err = buf;
             return LA_ERR_INVALID_ARG;

@@ -448,7 +448,9 @@ def engine_for(spec, run, state=None, options=None) -> Engine:
 def alch_pairs_static(x, q, sigma, epsilon, alch, excl_group, alch_idx, box, r_cut, eps_rf, coul, lam,
                       b_v, b_e, sc_alpha=0.5, sc_n=1, sc_m=1, forces=None, out=None, stream=None):
     """Marshal torch CUDA tensors into la_alch_pairs_static (no allocation
-    in the library; `forces` and `out` may be passed pre-allocated)."""
+    in the library; `forces` [n, 3] float32 and `out` [6] float64 may be
+    passed pre-allocated).  out = (dU/dlambda, dU/dlambda_v, dU/dlambda_e,
+    soft-core LJ energy, lambda_e RF energy, device status bits)."""
     import torch
 
     lib = load()
@@ -456,7 +458,9 @@ def alch_pairs_static(x, q, sigma, epsilon, alch, excl_group, alch_idx, box, r_c
     if forces is None:
         forces = torch.empty((n, 3), dtype=torch.float32, device=x.device)
     if out is None:
-        out = torch.empty(5, dtype=torch.float64, device=x.device)
+        out = torch.empty(6, dtype=torch.float64, device=x.device)
+    if tuple(forces.shape) != (n, 3) or out.numel() < 6:
+        raise ValueError("alch_pairs_static wants forces [n, 3] and out [6]")
     if stream is None:
         stream = torch.cuda.current_stream(x.device)
     ptr = lambda t: C.c_void_p(t.data_ptr())

@@ -123,3 +123,34 @@ def test_calls_reject_a_null_handle():
     assert lib.la_get_state(None, 0, labf._p(x), labf._p(x), None, None, None, None) == -1
     assert lib.la_set_state(None, 0, labf._p(x), labf._p(x), None, None, None) == -1
     assert lib.la_step_walkers(None, 1, None) == -1
+
+
+def test_soft_core_powers_below_one_are_rejected():
+    """n lambda_v^(n-1) at lambda_v = 0 and m (1 - lambda_v)^(m-1) at
+    lambda_v = 1 are 0 * inf for powers 0, so the soft-core family is
+    n, m >= 1: la_query_sizes and la_alch_pairs_static both reject smaller
+    powers on the host, before any device work."""
+    sp = synth.water_box(64, 4, box=1.25, r_cut=0.5)
+    run = synth.water_run(walkers_per_stage=1)
+    assert _query(synth.with_changes(sp, sc_n=1, sc_m=1), run)[0] == 0
+    assert _query(synth.with_changes(sp, sc_n=2, sc_m=2), run)[0] == 0
+    assert _query(synth.with_changes(sp, sc_n=0), run)[0] == -1
+    assert _query(synth.with_changes(sp, sc_m=0), run)[0] == -1
+    lib = labf.load()
+    buf = np.zeros(16, np.float64)  # never read: the call fails during validation
+    p = labf._p(buf)
+    for n_, m_ in ((0, 1), (1, 0), (-1, 1)):
+        rc = lib.la_alch_pairs_static(4, p, p, p, p, p, p, 1, p, 10.0, 1.0, 78.0, 1.0, 0.5, 0.5, 0.5, 0.5,
+                                      n_, m_, p, p, None)
+        assert rc == -1
+        assert b"soft-core powers" in lib.la_static_last_error()
+
+
+def test_oracle_rejects_soft_core_powers_below_one():
+    import oracle
+
+    sp = synth.water_box(64, 4, box=1.25, r_cut=0.5)
+    oracle.OracleSystem(synth.with_changes(sp, sc_n=2, sc_m=1))
+    for kw in (dict(sc_n=0), dict(sc_m=0)):
+        with pytest.raises(ValueError, match="soft-core powers"):
+            oracle.OracleSystem(synth.with_changes(sp, **kw))
