@@ -58,46 +58,71 @@ struct PairShared {
 // more work; the last one resets both for the next launch
 constexpr int CTR_ITEM = 4, CTR_DONE = 5;
 
-// i-forces of one flush: sum over the 4 j-lanes; lane (ia, jb) writes
-// i-clusters 2jb and 2jb+1; the accumulators restart from zero
+// i-forces of one flush, summed over the 4 j-lanes of each i-atom with a
+// transposed tree: at the first level (partner jb ^ 1) a lane keeps the
+// i-clusters {0, 1, 4, 5} (jb even) or {2, 3, 6, 7} (jb odd) and sends the
+// others; at the second (partner jb ^ 2) it keeps the lower or upper pair, so
+// lane (ia, jb) ends with i-clusters 2jb and 2jb + 1.  Every i-atom's sum is
+// (a0 + a1) + (a2 + a3) over the j-lanes.  The accumulators restart from zero.
 __device__ __forceinline__ void flush_i(const Dev &d, int gS, int ia, int jb, unsigned touched,
                                         float (&fi)[NIC][3]) {
+    const bool odd = (jb & 1) != 0, upper = (jb & 2) != 0;
+    float k1[4][3];
 #pragma unroll
-    for (int ic = 0; ic < NIC; ++ic) {
+    for (int t = 0; t < 4; ++t) {
+        const int ke = t < 2 ? t : t + 2;  // 0, 1, 4, 5
+        const int ko = ke + 2;             // 2, 3, 6, 7
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            fi[ic][c] += __shfl_xor_sync(FULL, fi[ic][c], 8);
-            fi[ic][c] += __shfl_xor_sync(FULL, fi[ic][c], 16);
+            const float keep = odd ? fi[ko][c] : fi[ke][c];
+            const float send = odd ? fi[ke][c] : fi[ko][c];
+            k1[t][c] = keep + __shfl_xor_sync(FULL, send, 8);
         }
     }
 #pragma unroll
-    for (int ic = 0; ic < NIC; ++ic) {
-        if ((ic >> 1) == jb && (touched & (1u << ic))) {
-            unsigned long long *p = d.F + 3 * (size_t)(gS + ic * IC + ia);
-            atomicAdd(p + 0, (unsigned long long)__float2ll_rn(fi[ic][0] * F_TO_FIX));
-            atomicAdd(p + 1, (unsigned long long)__float2ll_rn(fi[ic][1] * F_TO_FIX));
-            atomicAdd(p + 2, (unsigned long long)__float2ll_rn(fi[ic][2] * F_TO_FIX));
-        }
+    for (int t = 0; t < 2; ++t) {
+        const int ic = 2 * jb + t;
+        unsigned long long *p = d.F + 3 * (size_t)(gS + ic * IC + ia);
+        const bool on = (touched >> ic) & 1u;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) fi[ic][c] = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            const float keep = upper ? k1[t + 2][c] : k1[t][c];
+            const float send = upper ? k1[t][c] : k1[t + 2][c];
+            const float v = keep + __shfl_xor_sync(FULL, send, 16);
+            if (on) atomicAdd(p + c, f2fix(v));
+        }
     }
+#pragma unroll
+    for (int ic = 0; ic < NIC; ++ic) fi[ic][0] = fi[ic][1] = fi[ic][2] = 0.f;
 }
 
-// j-force of one entry (positive accumulation: the atom receives -c): sum
-// over the 8 i-lanes of each j-atom, transposed so that lanes ia = 0, 2, 4 of
-// the group end with x, y, z
-__device__ __forceinline__ void flush_j(const Dev &d, int gj, int ia, float fjx, float fjy, float fjz) {
-    const bool b2 = (ia & 4) != 0, b1 = (ia & 2) != 0;
-    const float p0 = b2 ? fjx : fjz, p1 = b2 ? fjy : 0.f;
-    const float q0 = __shfl_xor_sync(FULL, p0, 4);
-    const float q1 = __shfl_xor_sync(FULL, p1, 4);
-    const float a0 = (b2 ? fjz : fjx) + q0;
-    const float a1 = (b2 ? 0.f : fjy) + q1;
-    const float q2 = __shfl_xor_sync(FULL, b1 ? a0 : a1, 2);
-    float c = (b1 ? a1 : a0) + q2;
-    c += __shfl_xor_sync(FULL, c, 1);
-    if ((ia & 1) == 0 && ia < 6)
-        atomicAdd(d.F + 3 * (size_t)gj + (ia >> 1), (unsigned long long)__float2ll_rn(-c * F_TO_FIX));
+// j-forces of two entries A and B at once (B absent: pass zeros and
+// has_b = false).  Lane (ia, jb) holds j-atom jb's partial sums over its
+// i-atoms (a for A, b for B; positive accumulation, the atom receives minus
+// the sum).  Transposed tree over the 8 i-lanes: partner ia ^ 4 (lanes
+// ia < 4 keep A, the others B), ia ^ 2 (keep x, y or z, 0), ia ^ 1; lane ia
+// ends with A's component ia (ia < 3) or B's component ia - 4 (4 <= ia < 7).
+// Each sum is ((a0 + a4) + (a2 + a6)) + ((a1 + a5) + (a3 + a7)), whether or
+// not B is present.
+__device__ __forceinline__ void flush_j2(const Dev &d, int gjA, int gjB, bool has_b, int ia, const float (&a)[3],
+                                         const float (&b)[3]) {
+    const bool h4 = (ia & 4) != 0, h2 = (ia & 2) != 0, h1 = (ia & 1) != 0;
+    float v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float keep = h4 ? b[c] : a[c];
+        const float send = h4 ? a[c] : b[c];
+        v[c] = keep + __shfl_xor_sync(FULL, send, 4);
+    }
+    // (x, y) kept by h2 = 0, (z, 0) by h2 = 1
+    const float k0 = h2 ? v[2] : v[0], k1 = h2 ? 0.f : v[1];
+    const float s0 = h2 ? v[0] : v[2], s1 = h2 ? v[1] : 0.f;
+    const float w0 = k0 + __shfl_xor_sync(FULL, s0, 2);
+    const float w1 = k1 + __shfl_xor_sync(FULL, s1, 2);
+    const float kk = h1 ? w1 : w0, ss = h1 ? w0 : w1;
+    const float c = kk + __shfl_xor_sync(FULL, ss, 1);
+    const int comp = ia & 3;
+    if (comp < 3 && (!h4 || has_b)) atomicAdd(d.F + 3 * (size_t)(h4 ? gjB : gjA) + comp, f2fix(-c));
 }
 
 // One work item's entries, prepared and evaluated 32 at a time; the
@@ -148,11 +173,13 @@ __device__ __forceinline__ void item_entries(const Dev &d, PairShared<WARPS> &sh
             dst[0] = src[0];
             dst[1] = src[1];
         }
+        // entries whose tiles were all pruned add nothing: skip them
+        unsigned emask = __ballot_sync(FULL, im_l != 0u);
         __syncwarp();
-        // one entry: every flagged i-cluster against the entry's j-cluster
-        auto entry = [&](int k) {
+        // one entry: every flagged i-cluster against the entry's j-cluster;
+        // fjs receives j-atom jb's partial force over this lane's i-atoms
+        auto entry = [&](int k, float (&fjs)[3]) {
             const unsigned imask = __shfl_sync(FULL, im_l, k);
-            const int gj = __shfl_sync(FULL, gj_l, k) + jb;
             const float4 xj = sh.jx[wib][k][jb];
             const float2 lj_j = sh.jl[wib][k][jb];
             const unsigned lb = sh.lb[wib][k][lane];
@@ -197,18 +224,31 @@ __device__ __forceinline__ void item_entries(const Dev &d, PairShared<WARPS> &sh
                 const unsigned keep = __reduce_or_sync(FULL, kb);
                 keep_l = lane == k ? keep : keep_l;
             }
-            flush_j(d, gj, ia, fj[0][0] + fj[1][0], fj[0][1] + fj[1][1], fj[0][2] + fj[1][2]);
+            fjs[0] = fj[0][0] + fj[1][0];
+            fjs[1] = fj[0][1] + fj[1][1];
+            fjs[2] = fj[0][2] + fj[1][2];
         };
         // two entries per iteration: the compiler interleaves their
-        // independent loads and arithmetic (the order of every sum stays);
-        // the pruning form, which holds more registers, takes one
-        int k = 0;
-        if (!PRUNE)
-            for (; k + 1 < ne; k += 2) {
-                entry(k);
-                entry(k + 1);
+        // independent loads and arithmetic (the order of every sum stays), and
+        // one transposed reduction serves both j-clusters
+        while (emask) {
+            const int k0 = __ffs(emask) - 1;
+            emask &= emask - 1u;
+            float a[3], b[3] = {0.f, 0.f, 0.f};
+            const int gA = __shfl_sync(FULL, gj_l, k0) + jb;
+            int gB = 0;
+            const bool two = emask != 0u;
+            if (!PRUNE && two) {
+                const int k1 = __ffs(emask) - 1;
+                emask &= emask - 1u;
+                gB = __shfl_sync(FULL, gj_l, k1) + jb;
+                entry(k0, a);
+                entry(k1, b);
+            } else {
+                entry(k0, a);
             }
-        for (; k < ne; ++k) entry(k);
+            flush_j2(d, gA, gB, !PRUNE && two, ia, a, b);
+        }
         flush_i(d, gS, ia, jb, touched, fi);  // every 32 entries (EPC)
         touched = 0;
         if (PRUNE && lane < ne) d.ent_hdr[ebase + eb + lane].y = (hy_l & ~0xff00) | (int)(keep_l << 8);
@@ -317,7 +357,7 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
     return r;
 }
 
-constexpr int EPC2 = 16;  // entries prepared per pass in the packed variant
+constexpr int EPC2 = 16;  // entries prepared per pass in the packed variant (two per i-flush)
 
 template <int WARPS>
 struct PairShared2 {
@@ -330,7 +370,11 @@ struct PairShared2 {
     int pre[LA_MAX_WALKERS_PER_LAUNCH + 1];
 };
 
-// one work item of the packed form (PRUNE as in item_entries)
+// one work item of the packed form (PRUNE as in item_entries).  Per entry the
+// lane's j-atom is read once (three packed registers pairs of duplicated
+// values); per flagged i-cluster pair one unit evaluates the lane's pairs with
+// i-clusters 2p and 2p+1 together, each packed operation rounding per half as
+// its scalar counterpart, so the sums equal the scalar variants' bit for bit.
 template <int WARPS, int MSHIFT, bool PRUNE>
 __device__ __forceinline__ void item_entries_x2(const Dev &d, PairShared2<WARPS> &sh, const SysDev &S, int4 it,
                                                 int gS) {
@@ -372,11 +416,14 @@ __device__ __forceinline__ void item_entries_x2(const Dev &d, PairShared2<WARPS>
             dst[0] = src[0];
             dst[1] = src[1];
         }
+        unsigned emask = __ballot_sync(FULL, im_l != 0u);  // entries with tiles left
         __syncwarp();
-        auto entry = [&](int k) {
+        auto entry = [&](int k, float (&fjs)[3]) {
             const unsigned imask = __shfl_sync(FULL, im_l, k);
-            const int gj = __shfl_sync(FULL, gj_l, k) + jb;
             const unsigned lb = sh.lb[wib][k][lane];
+            const float4 J0 = sh.sj[wib][k][jb][0], J1 = sh.sj[wib][k][jb][1], J2 = sh.sj[wib][k][jb][2];
+            const f32x2 xj = pk(J0.x, J0.y), yj = pk(J0.z, J0.w), zj = pk(J1.x, J1.y);
+            const f32x2 qj = pk(J1.z, J1.w), sgj = pk(J2.x, J2.y), ej = pk(J2.z, J2.w);
             touched |= imask;
             f32x2 fjx = 0ull, fjy = 0ull, fjz = 0ull;  // (even, odd) i-clusters
             unsigned kb = 0;  // this lane's pairs within r_c + margin, per i-cluster
@@ -385,22 +432,18 @@ __device__ __forceinline__ void item_entries_x2(const Dev &d, PairShared2<WARPS>
                 if (imask & (3u << (2 * p))) {
                     const float4 I0 = sh.si[wib][p][ia][0], I1 = sh.si[wib][p][ia][1];
                     const float4 I2 = sh.si[wib][p][ia][2];
-                    // j operands re-read per i-cluster pair: keeps 12 registers free
-                    const float4 J0 = sh.sj[wib][k][jb][0], J1 = sh.sj[wib][k][jb][1];
-                    const float4 J2 = sh.sj[wib][k][jb][2];
-                    const f32x2 xj = pk(J0.x, J0.y), yj = pk(J0.z, J0.w), zj = pk(J1.x, J1.y);
-                    const f32x2 qj = pk(J1.z, J1.w), sgj = pk(J2.x, J2.y), ej = pk(J2.z, J2.w);
                     const f32x2 dx = sub2(pk(I0.x, I0.y), xj);
                     const f32x2 dy = sub2(pk(I0.z, I0.w), yj);
                     const f32x2 dz = sub2(pk(I1.x, I1.y), zj);
                     const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
                     const float2 r2s = upk(r2);
+                    const bool la = (lb >> (2 * p)) & 1u, lbb = (lb >> (2 * p + 1)) & 1u;
                     if (PRUNE) {
-                        kb |= (((lb >> (2 * p)) & 1u) && r2s.x < rp2) ? 1u << (2 * p) : 0u;
-                        kb |= (((lb >> (2 * p + 1)) & 1u) && r2s.y < rp2) ? 2u << (2 * p) : 0u;
+                        kb |= (la && r2s.x < rp2) ? 1u << (2 * p) : 0u;
+                        kb |= (lbb && r2s.y < rp2) ? 2u << (2 * p) : 0u;
                     }
-                    const bool ina = ((lb >> (2 * p)) & 1u) && (r2s.x < rc2);
-                    const bool inb = ((lb >> (2 * p + 1)) & 1u) && (r2s.y < rc2);
+                    const bool ina = la && (r2s.x < rc2);
+                    const bool inb = lbb && (r2s.y < rc2);
                     const f32x2 rinv = pk(rsqrtf(r2s.x), rsqrtf(r2s.y));
                     const f32x2 r2inv = mul2(rinv, rinv);
                     const f32x2 sg = add2(pk(I2.x, I2.y), sgj);
@@ -428,15 +471,29 @@ __device__ __forceinline__ void item_entries_x2(const Dev &d, PairShared2<WARPS>
                 keep_l = lane == k ? keep : keep_l;
             }
             const float2 jx = upk(fjx), jy = upk(fjy), jz = upk(fjz);
-            flush_j(d, gj, ia, jx.x + jx.y, jy.x + jy.y, jz.x + jz.y);
+            fjs[0] = jx.x + jx.y;
+            fjs[1] = jy.x + jy.y;
+            fjs[2] = jz.x + jz.y;
         };
-        int k = 0;
-        for (; k + 1 < ne; k += 2) {
-            entry(k);
-            entry(k + 1);
+        while (emask) {
+            const int k0 = __ffs(emask) - 1;
+            emask &= emask - 1u;
+            float a[3], b[3] = {0.f, 0.f, 0.f};
+            const int gA = __shfl_sync(FULL, gj_l, k0) + jb;
+            int gB = 0;
+            const bool two = emask != 0u;
+            if (!PRUNE && two) {
+                const int k1 = __ffs(emask) - 1;
+                emask &= emask - 1u;
+                gB = __shfl_sync(FULL, gj_l, k1) + jb;
+                entry(k0, a);
+                entry(k1, b);
+            } else {
+                entry(k0, a);
+            }
+            flush_j2(d, gA, gB, !PRUNE && two, ia, a, b);
         }
-        if (k < ne) entry(k);
-        // flush the i-forces at the same 32-entry boundaries as the scalar variants
+        // the i-forces at the same 32-entry boundaries as the scalar variants
         if (((eb - it.y) & 31) == 32 - EPC2 || eb + EPC2 >= it.z) {
             float fs[NIC][3];
 #pragma unroll
