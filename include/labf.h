@@ -63,6 +63,7 @@ extern "C" {
 #define LA_STATUS_COLUMN_OVERFLOW 0x8u
 #define LA_STATUS_ALCH_OVERFLOW 0x10u
 #define LA_STATUS_BAD_INDEX 0x20u /* la_alch_pairs_static: alch_idx entry not an alchemical atom */
+#define LA_STATUS_BAD_PARAM 0x40u /* la_energy_forces_device: negative or non-finite epsilon, sigma, q */
 
 /* ---- energy terms reported by la_energy_forces ---- */
 #define LA_PAIR_VARIANTS 6
@@ -261,34 +262,89 @@ int la_energy_forces(la_handle *h, int walker, uint32_t flags, double *energy_te
                      void *stream);
 
 /*
+ * la_energy_forces_device: the same evaluation with every input and output in
+ * device memory and no host synchronisation (for the differentiation path:
+ * U(x, lambda, theta) and its hand-written derivatives, north-star
+ * extension; the paper does not differentiate with respect to force-field
+ * parameters).  x (device [n_atoms][3] float32, atom order, or NULL: keep
+ * the walker's positions) replaces the walker's positions and its lists are
+ * rebuilt from them (recomputed, not stored); theta (device [n_alch][3]
+ * double: epsilon, sigma, q of each alchemical atom in index order, or NULL)
+ * replaces the system's alchemical parameters for all its walkers (the other
+ * walkers are refreshed before their next use); lam (device double, or
+ * NULL) replaces the walker's lambda.  out (device double, or NULL) receives
+ * [LA_N_TERMS] energy terms, U, dU/dlambda, dU/dtheta [P] and
+ * d2U/dlambda dtheta [P] (P = 3 n_alch + 1, the last entry k1 of the
+ * lambda-switched well); forces (device [n_atoms][3] float32, or NULL)
+ * receives -dU/dx.  Asynchronous on `stream`: a device error (including
+ * LA_STATUS_BAD_PARAM for negative or non-finite epsilon or sigma, which
+ * leaves those atoms' parameters unchanged) is reported by the next call.
+ */
+int la_energy_forces_device(la_handle *h, int walker, const float *x, const double *theta,
+                            const double *lam, double *out, float *forces, void *stream);
+
+/*
  * la_get_state / la_set_state: positions, velocities (host [n][3] float32),
  * lambda and p_lambda (host double) and the step counter of one walker, in
- * the system's atom order.  After la_set_state the walker's lists and
- * forces (no sample is folded) are rebuilt once, for every walker set since,
- * before the next call that needs them (la_step_walkers[_plain],
- * la_energy_forces, la_get_pairs, la_time_kernels, la_autotune,
- * la_abf_import), so that setting all walkers costs one refresh.  Any
- * pointer may be NULL (left unchanged / not read).  Synchronising.
+ * the system's atom order.  The step counter is the counter of the walker's
+ * Philox streams (SI S1 BAOAB noise): setting it back repeats the noise of
+ * that step.  After la_set_state the walker's lists and forces (no sample is
+ * folded) are rebuilt once, for every walker set since, before the next call
+ * that needs them (la_step_walkers[_plain], la_energy_forces, la_get_pairs,
+ * la_time_kernels, la_autotune, la_abf_import, la_checkpoint_save), so that
+ * setting all walkers costs one refresh.  Any pointer may be NULL (left
+ * unchanged / not read).  If a copy fails part way, the walker may hold part
+ * of the new state and the handle goes into the sticky error state.
+ * Synchronising.
  */
 int la_get_state(la_handle *h, int walker, float *x, float *v, double *lam, double *plam,
                  uint64_t *step, void *stream);
 int la_set_state(la_handle *h, int walker, const float *x, const float *v, const double *lam,
-                 const double *plam, void *stream);
+                 const double *plam, const uint64_t *step, void *stream);
 
 /*
  * la_get_states / la_set_states: the same for every walker at once, with one
  * synchronisation per call.  x and v (host float32) hold the walkers one
  * after another in handle order, walker w's [n_atoms][3] block starting at
- * 3 * (sum of n_atoms over walkers < w); lam and plam (host double) hold one
- * value per walker; any pointer may be NULL (left unchanged / not read).
- * Page-locked buffers are copied by DMA, others through the driver's
- * staging.  After la_set_states every walker's lists and forces are
- * refreshed before the next call that needs them, as after la_set_state.
+ * 3 * (sum of n_atoms over walkers < w); lam, plam (host double) and step
+ * (host uint64) hold one value per walker; any pointer may be NULL (left
+ * unchanged / not read).  Only page-locked host buffers are copied by DMA
+ * without intermediate waits; pageable buffers go through the driver's
+ * staging, which waits for each copy.  After la_set_states every walker's
+ * lists and forces are refreshed before the next call that needs them, as
+ * after la_set_state (a failed copy leaves the handle in the sticky error
+ * state).  Synchronising.
+ */
+int la_get_states(la_handle *h, float *x, float *v, double *lam, double *plam, uint64_t *step,
+                  void *stream);
+int la_set_states(la_handle *h, const float *x, const float *v, const double *lam, const double *plam,
+                  const uint64_t *step, void *stream);
+
+/*
+ * la_checkpoint_save / la_checkpoint_load: the engine's complete state (every
+ * walker's atoms in their current slot order, neighbour lists, pruning state,
+ * forces, lambda particles, step counters, ABF accumulators shared and
+ * unmerged, theta statistics, counters) as one host byte image, for exact
+ * restarts (SI S1: runs are continued from saved states).  A run restored
+ * from a checkpoint into an engine created from the same inputs and options
+ * continues bit for bit as the run that saved it would have.
+ *
+ * la_checkpoint_save: *bytes receives the image size (a header plus the
+ * state part of the arena, a few hundred MB for 16 walkers of 12 300 atoms);
+ * with buf = NULL nothing else happens.  Otherwise buf (host, caller-owned,
+ * cap bytes, page-locked for a fast copy) receives the image.  Refreshes
+ * pending lists first (after la_set_state).  Errors: LA_ERR_INVALID_ARG when
+ * cap is too small, LA_ERR_STATE after a device error.  Synchronising.
+ *
+ * la_checkpoint_load: replace the engine's state with an image.  The engine
+ * must have been created from the same systems, run parameters and options
+ * (the header's fingerprint of the layout and parameters and its
+ * chunk_entries must match; LA_ERR_INVALID_ARG otherwise, with nothing
+ * changed).  Clears a sticky error state if the image is clean.
  * Synchronising.
  */
-int la_get_states(la_handle *h, float *x, float *v, double *lam, double *plam, void *stream);
-int la_set_states(la_handle *h, const float *x, const float *v, const double *lam, const double *plam,
-                  void *stream);
+int la_checkpoint_save(la_handle *h, void *buf, size_t cap, size_t *bytes, void *stream);
+int la_checkpoint_load(la_handle *h, const void *buf, size_t bytes, void *stream);
 
 /*
  * la_set_alch_params: replace (epsilon, sigma, charge) of the alchemical
@@ -354,15 +410,20 @@ int la_sync(la_handle *h, void *stream, uint32_t *status_bits);
 int la_stats(la_handle *h, int64_t *out, void *stream);
 
 /*
- * la_time_kernels: run n_steps batched steps outside the graph, the same
- * launches as the graph's, with CUDA events between them on `stream`;
- * ms_out (host [LA_N_KERNELS]) receives the mean device milliseconds per
- * step of each kernel class, launches_out (host [LA_N_KERNELS], may be NULL)
- * the launch counts.  In the batched step the bonded terms, the walker terms
- * and the lambda update run inside the pair launch, so their classes read 0
- * and "pairs" is the whole fused launch.  Synchronising.
+ * la_time_kernels: run n_steps batched steps outside the graph with CUDA
+ * events between the launches on `stream`, in the order and with the
+ * conditions of the graph's step: the integrator, the gate kernel, the list
+ * kernels only on steps where some walker must rebuild (the host reads the
+ * walkers' rebuild flags after the gate, as the graph's conditional node
+ * does on the device), and the fused pair launch.  ms_out (host
+ * [LA_N_KERNELS]) receives the mean device milliseconds per MD step of each
+ * class (so that integrate + rebuild + pairs is the step's kernel time, the
+ * list kernels averaged over the steps at the rebuild rate met), and
+ * launches_out (host [LA_N_KERNELS], may be NULL) the launch counts.  In the
+ * batched step the bonded terms, the walker terms and the lambda update run
+ * inside the pair launch, so their classes read 0.  Synchronising.
  */
-#define LA_N_KERNELS 6 /* integrate, rebuild (gate + list kernels), pairs, bonded, walker, lambda */
+#define LA_N_KERNELS 6 /* integrate, rebuild (gate + list kernels when due), pairs, bonded, walker, lambda */
 int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_out, void *stream);
 
 /*
@@ -376,6 +437,17 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
  * Synchronising.
  */
 int la_autotune(la_handle *h, void *stream);
+
+/*
+ * la_fp_peak: measured fused-multiply-add rate of this GPU (the current
+ * device), in TFLOP/s (an FMA counts 2): fp64 = 0 for FP32 (the CUDA-core
+ * peak the pair pass's roofline is taken against), 1 for FP64.  Runs
+ * independent FMA chains on every SM for about `seconds` (0 < seconds <= 10)
+ * of device time after a warm-up, timed with CUDA events on `stream`.  A
+ * measurement aid for the roofline (the paper has no counterpart).
+ * Synchronising.  Errors: LA_ERR_INVALID_ARG, LA_ERR_CUDA.
+ */
+int la_fp_peak(int fp64, double seconds, double *tflops, void *stream);
 
 /* la_autotune_report: text describing the chosen launch shapes (static buffer). */
 const char *la_autotune_report(la_handle *h);

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblabf.so")
-SOURCES = ["labf_api.cu", "k_dyn.cu", "k_list.cu", "k_pairs.cu", "k_io.cu", "k_static.cu"]
+SOURCES = ["labf_api.cu", "k_dyn.cu", "k_list.cu", "k_pairs.cu", "k_io.cu", "k_static.cu", "k_peak.cu"]
 HEADERS = ["labf_internal.cuh", "labf_launch.h", "labf_dyn.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz=true: FP32 denormals flush to zero (MD forces and positions never need

@@ -151,8 +151,38 @@ void compute_layout(const la_system_desc *sys, int n_sys, const la_options *opt,
         const double wc = S.box / sl.ncx;
         const double h = std::min(S.box, 64.0 / (sl.rho * wc * wc));
         const double ej = std::cbrt(4.0 / sl.rho);
+        // columns of the starting structures: the sparsest non-empty column
+        // holds the tallest super-cluster (a lattice start can leave a column
+        // with a thin sliver of atoms, whose one super-cluster spans the
+        // whole box height), the densest one the most j-clusters in reach
+        int cmin = 1 << 30, cmax = 0;
+        {
+            std::vector<int> cnt(sl.n_cols);
+            const double binv = 1.0 / S.box;
+            for (int w = 0; w < sl.W; ++w) {
+                std::fill(cnt.begin(), cnt.end(), 0);
+                for (int i = 0; i < S.n_atoms; ++i) {
+                    int c2[2];
+                    for (int q = 0; q < 2; ++q) {
+                        const double t = (double)S.x0[3 * ((size_t)w * S.n_atoms + i) + q] * binv;
+                        double f = (t - std::floor(t)) * 16777216.0;
+                        unsigned long long u = (unsigned long long)std::floor(f);
+                        if (u >= 16777216ull) u = 0;
+                        c2[q] = (int)((u * (unsigned long long)sl.ncx) >> 24);
+                    }
+                    ++cnt[c2[0] + sl.ncx * c2[1]];
+                }
+                for (int c : cnt) {
+                    if (c > 0) cmin = std::min(cmin, c);
+                    cmax = std::max(cmax, c);
+                }
+            }
+        }
+        const double h_tall = cmax > 0 ? std::min(S.box, std::max(h, SC * S.box / (double)cmin)) : h;
+        const double rho_dense = std::max(sl.rho, cmax / (wc * wc * S.box));
         const double V = steiner_box(wc + ej, wc + ej, h + ej, sl.r_list);
-        const double full = std::min(sl.rho * V / JC, 27.0 * sl.sc_cap * NJC);
+        const double V_tall = steiner_box(wc + ej, wc + ej, h_tall + ej, sl.r_list);
+        const double full = std::min(std::max(sl.rho * V, rho_dense * V_tall) / JC, 27.0 * sl.sc_cap * NJC);
         ent_est = std::max(ent_est, full);
         // list radius in quantized units and the candidate columns per
         // dimension: a super-cluster box lies inside one column, so at most
@@ -160,8 +190,9 @@ void compute_layout(const la_system_desc *sys, int n_sys, const la_options *opt,
         sl.Rq = (int)std::ceil(sl.r_list / S.box * 16777216.0) + 1;
         sl.cspan = (int)std::floor(3.0 + 2.0 * sl.Rq * (double)sl.ncx / 16777216.0);
         L.ncs = std::max(L.ncs, sl.cspan * sl.cspan);
-        const double col_jc = sl.rho * wc * wc * (h + 2.0 * sl.r_list + 2.0 * ej) / JC;
-        const double col_cap = 3.0 * NJC * (sl.rho * wc * wc * S.box / SC + 2.0);
+        const double col_jc = std::max(sl.rho * wc * wc * (h + 2.0 * sl.r_list + 2.0 * ej),
+                                       rho_dense * wc * wc * (h_tall + 2.0 * sl.r_list + 2.0 * ej)) / JC;
+        const double col_cap = 3.0 * NJC * (std::max(sl.rho * wc * wc * S.box, (double)cmax) / SC + 2.0);
         sub_est = std::max(sub_est, std::min(col_jc, col_cap));
         alch_est = std::max(alch_est, sl.rho * 4.0 / 3.0 * pi * std::pow(sl.r_list, 3));
         L.sys.push_back(sl);
@@ -197,8 +228,11 @@ void compute_layout(const la_system_desc *sys, int n_sys, const la_options *opt,
 }
 
 // carve every device array out of the arena (dry run when base == nullptr)
+// Arrays that carry the engine's state come first; the rebuild chain's and
+// the list builder's scratch and the host I/O staging area come last, so that
+// the state is the prefix [0, *state_bytes) (what a checkpoint copies).
 size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io_floats,
-             SysDev **sysd, WalkerDev **walkd, StageDev **staged) {
+             SysDev **sysd, WalkerDev **walkd, StageDev **staged, size_t *state_bytes = nullptr) {
     Arena a{base, 0, cap, base == nullptr};
     *sysd = a.take<SysDev>(L.sys.size());
     *walkd = a.take<WalkerDev>(L.W);
@@ -232,13 +266,6 @@ size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io
     d.uq = a.take<int4>(L.slots);
     d.smeta = a.take<int2>(L.slots);
     d.sexcl = a.take<int4>(L.slots);
-    d.t_xq = a.take<float4>(L.slots);
-    d.t_vv = a.take<float4>(L.slots);
-    d.t_old = a.take<int>(L.slots);
-    d.t_uq = a.take<int4>(L.slots);
-    d.t_col = a.take<int>(L.slots);
-    d.t_pos = a.take<int>(L.slots);
-    d.bucket = a.take<int>(L.atoms_w);
     d.slot_of_atom = a.take<int>(L.atoms_w);
     d.col_count = a.take<int>(L.cols);
     d.col_start = a.take<int>(L.cols);
@@ -253,9 +280,6 @@ size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io
     d.sc_nent = a.take<int>(L.scs);
     d.ent_hdr = a.take<int2>(L.scs * (long long)L.ent_cap);
     d.ent_lb = a.take<unsigned char>(32 * L.scs * (long long)L.ent_cap);
-    d.sub_hdr = a.take<int2>(L.scs * (long long)L.ncs * L.sub_cap);
-    d.sub_lb = a.take<unsigned char>(32 * L.scs * (long long)L.ncs * L.sub_cap);
-    d.sub_n = a.take<int>(L.scs * (long long)L.ncs);
     d.items = a.take<int4>(L.items);
     d.n_items = a.take<int>(L.W);
     d.alch_cnt = a.take<int>(std::max<long long>(1, L.alch_w));
@@ -287,6 +311,18 @@ size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io
     d.counters = a.take<unsigned long long>(16);
     d.wdone = a.take<unsigned int>(L.W);
     d.sdone = a.take<unsigned int>(L.n_stages);
+    if (state_bytes) *state_bytes = (a.off + ALIGN - 1) / ALIGN * ALIGN;
+    // scratch: rewritten before every use
+    d.t_xq = a.take<float4>(L.slots);
+    d.t_vv = a.take<float4>(L.slots);
+    d.t_old = a.take<int>(L.slots);
+    d.t_uq = a.take<int4>(L.slots);
+    d.t_col = a.take<int>(L.slots);
+    d.t_pos = a.take<int>(L.slots);
+    d.bucket = a.take<int>(L.atoms_w);
+    d.sub_hdr = a.take<int2>(L.scs * (long long)L.ncs * L.sub_cap);
+    d.sub_lb = a.take<unsigned char>(32 * L.scs * (long long)L.ncs * L.sub_cap);
+    d.sub_n = a.take<int>(L.scs * (long long)L.ncs);
     const int iof = std::max(IO_FLOATS_MIN, 8 * L.max_n);
     *io = a.take<float>(iof);
     *io_floats = iof;
@@ -320,6 +356,8 @@ struct la_handle {
     long long steps = 0, launches = 0, launches_per_step = 0;
     std::string err, report;
     bool dirty = false;  // a walker's state was set: lists and forces are refreshed lazily
+    void *arena = nullptr;
+    size_t state_bytes = 0;  // arena prefix holding the engine's state (checkpoints)
 };
 
 namespace {
@@ -347,6 +385,7 @@ int status_to_code(unsigned bits) {
         return LA_ERR_LIST_OVERFLOW;
     if (bits & LA_STATUS_FIXED_OVERFLOW) return LA_ERR_FIXED_OVERFLOW;
     if (bits & LA_STATUS_NONFINITE) return LA_ERR_NONFINITE;
+    if (bits & LA_STATUS_BAD_PARAM) return LA_ERR_INVALID_ARG;
     return LA_OK;
 }
 
@@ -356,6 +395,7 @@ const char *status_text(unsigned bits) {
     if (bits & LA_STATUS_LIST_OVERFLOW) return "the cluster-pair list exceeded its capacity";
     if (bits & LA_STATUS_FIXED_OVERFLOW) return "a force exceeded the fixed-point range";
     if (bits & LA_STATUS_NONFINITE) return "non-finite positions or lambda";
+    if (bits & LA_STATUS_BAD_PARAM) return "negative or non-finite alchemical parameters";
     return "ok";
 }
 
@@ -658,7 +698,9 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
     SysDev *d_sys;
     WalkerDev *d_walk;
     StageDev *d_stage;
-    size_t need = carve(L, (char *)arena, arena_bytes, h->d, &h->io, &h->io_floats, &d_sys, &d_walk, &d_stage);
+    size_t need = carve(L, (char *)arena, arena_bytes, h->d, &h->io, &h->io_floats, &d_sys, &d_walk, &d_stage,
+                        &h->state_bytes);
+    h->arena = arena;
     *out = h;
     if (!arena || need > arena_bytes || ((uintptr_t)arena % ALIGN) != 0)
         return fail(h, LA_ERR_ARENA_TOO_SMALL, "arena of %zu bytes (need %zu, 256-byte aligned)", arena_bytes, need);
@@ -1107,6 +1149,32 @@ int la_energy_forces(la_handle *h, int walker, uint32_t flags, double *energy_te
     return LA_OK;
 }
 
+int la_energy_forces_device(la_handle *h, int walker, const float *x, const double *theta, const double *lam,
+                            double *out, float *forces, void *stream) {
+    if (!h) return LA_ERR_INVALID_ARG;
+    if (walker < 0 || walker >= h->L.W) return fail(h, LA_ERR_INVALID_ARG, "bad walker");
+    int rc = check_posted(h);
+    if (rc != LA_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = flush_dirty(h, s);
+    if (rc != LA_OK) return rc;
+    const WalkerDev &W = h->walk[walker];
+    const SysDev &S = h->sys[W.sys];
+    if (theta) {
+        launch_alch_params_in(h->d, W.sys, S.n_alch, theta, s);
+        h->dirty = true;  // the system's other walkers refresh before their next use
+    }
+    if (x) launch_positions_in(h->d, walker, S.n_atoms, x, s);
+    if (lam) CU(h, cudaMemcpyAsync(h->d.lam + walker, lam, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    rc = prime(h, walker, walker + 1, false, true, s);
+    if (rc != LA_OK) return rc;
+    if (forces) launch_forces_out(h->d, walker, S.n_atoms, forces, s);
+    if (out) launch_ef_out(h->d, walker, S.P, out, s);
+    CU(h, cudaGetLastError());
+    post_status(h, s);
+    return LA_OK;
+}
+
 int la_get_state(la_handle *h, int walker, float *x, float *v, double *lam, double *plam, uint64_t *step,
                  void *stream) {
     if (!h) return LA_ERR_INVALID_ARG;
@@ -1132,29 +1200,38 @@ int la_get_state(la_handle *h, int walker, float *x, float *v, double *lam, doub
 }
 
 int la_set_state(la_handle *h, int walker, const float *x, const float *v, const double *lam, const double *plam,
-                 void *stream) {
+                 const uint64_t *step, void *stream) {
     if (!h) return LA_ERR_INVALID_ARG;
     if (walker < 0 || walker >= h->L.W) return fail(h, LA_ERR_INVALID_ARG, "bad walker");
     if (h->sticky != LA_OK) return fail(h, LA_ERR_STATE, "handle in error state: %s", h->err.c_str());
     cudaStream_t s = (cudaStream_t)stream;
     const int n = h->sys[h->walk[walker].sys].n_atoms;
     float *io = (float *)h->io;
-    if (x || v) {
-        // read back the current state first when one of the two stays unchanged
-        if (!x || !v) launch_state_io(h->d, walker, n, io, io + 3 * (size_t)n, false, s);
-        if (x) CU(h, cudaMemcpyAsync(io, x, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
-        if (v) CU(h, cudaMemcpyAsync(io + 3 * (size_t)n, v, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
-        launch_state_io(h->d, walker, n, io, io + 3 * (size_t)n, true, s);
-    }
-    if (lam) CU(h, cudaMemcpyAsync(h->d.lam + walker, lam, sizeof(double), cudaMemcpyHostToDevice, s));
-    if (plam) CU(h, cudaMemcpyAsync(h->d.plam + walker, plam, sizeof(double), cudaMemcpyHostToDevice, s));
+    // the walker's lists and forces are stale from here on, whatever follows
     static const int one = 1;
-    CU(h, cudaMemcpyAsync(h->d.rebuild + walker, &one, sizeof(int), cudaMemcpyHostToDevice, s));
     h->dirty = true;
+    int rc = [&]() -> int {
+        CU(h, cudaMemcpyAsync(h->d.rebuild + walker, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+        if (x || v) {
+            // read back the current state first when one of the two stays unchanged
+            if (!x || !v) launch_state_io(h->d, walker, n, io, io + 3 * (size_t)n, false, s);
+            if (x) CU(h, cudaMemcpyAsync(io, x, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+            if (v) CU(h, cudaMemcpyAsync(io + 3 * (size_t)n, v, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+            launch_state_io(h->d, walker, n, io, io + 3 * (size_t)n, true, s);
+        }
+        if (lam) CU(h, cudaMemcpyAsync(h->d.lam + walker, lam, sizeof(double), cudaMemcpyHostToDevice, s));
+        if (plam) CU(h, cudaMemcpyAsync(h->d.plam + walker, plam, sizeof(double), cudaMemcpyHostToDevice, s));
+        if (step) CU(h, cudaMemcpyAsync(h->d.step + walker, step, sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+        return LA_OK;
+    }();
+    if (rc != LA_OK) {  // the walker may hold part of the new state
+        h->sticky = rc;
+        return rc;
+    }
     return sync_status(h, s, nullptr);
 }
 
-int la_get_states(la_handle *h, float *x, float *v, double *lam, double *plam, void *stream) {
+int la_get_states(la_handle *h, float *x, float *v, double *lam, double *plam, uint64_t *step, void *stream) {
     if (!h) return LA_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int W = h->L.W;
@@ -1173,35 +1250,120 @@ int la_get_states(la_handle *h, float *x, float *v, double *lam, double *plam, v
     }
     if (lam) CU(h, cudaMemcpyAsync(lam, h->d.lam, sizeof(double) * W, cudaMemcpyDeviceToHost, s));
     if (plam) CU(h, cudaMemcpyAsync(plam, h->d.plam, sizeof(double) * W, cudaMemcpyDeviceToHost, s));
+    if (step) CU(h, cudaMemcpyAsync(step, h->d.step, sizeof(uint64_t) * W, cudaMemcpyDeviceToHost, s));
     CU(h, cudaStreamSynchronize(s));
     return LA_OK;
 }
 
 int la_set_states(la_handle *h, const float *x, const float *v, const double *lam, const double *plam,
-                  void *stream) {
+                  const uint64_t *step, void *stream) {
     if (!h) return LA_ERR_INVALID_ARG;
     if (h->sticky != LA_OK) return fail(h, LA_ERR_STATE, "handle in error state: %s", h->err.c_str());
     cudaStream_t s = (cudaStream_t)stream;
     const int W = h->L.W;
     float *io = (float *)h->io;
-    size_t off = 0;
-    for (int w = 0; w < W; ++w) {
-        const int n = h->sys[h->walk[w].sys].n_atoms;
-        if (x || v) {
-            // read back the current state first when one of the two stays unchanged
-            if (!x || !v) launch_state_io(h->d, w, n, io, io + 3 * (size_t)n, false, s);
-            if (x) CU(h, cudaMemcpyAsync(io, x + off, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
-            if (v) CU(h, cudaMemcpyAsync(io + 3 * (size_t)n, v + off, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
-            launch_state_io(h->d, w, n, io, io + 3 * (size_t)n, true, s);
-        }
-        off += 3 * (size_t)n;
-    }
-    if (lam) CU(h, cudaMemcpyAsync(h->d.lam, lam, sizeof(double) * W, cudaMemcpyHostToDevice, s));
-    if (plam) CU(h, cudaMemcpyAsync(h->d.plam, plam, sizeof(double) * W, cudaMemcpyHostToDevice, s));
     std::vector<int> one(W, 1);
-    CU(h, cudaMemcpyAsync(h->d.rebuild, one.data(), sizeof(int) * W, cudaMemcpyHostToDevice, s));
+    // every walker's lists and forces are stale from here on, whatever follows
     h->dirty = true;
+    int rc = [&]() -> int {
+        CU(h, cudaMemcpyAsync(h->d.rebuild, one.data(), sizeof(int) * W, cudaMemcpyHostToDevice, s));
+        size_t off = 0;
+        for (int w = 0; w < W; ++w) {
+            const int n = h->sys[h->walk[w].sys].n_atoms;
+            if (x || v) {
+                // read back the current state first when one of the two stays unchanged
+                if (!x || !v) launch_state_io(h->d, w, n, io, io + 3 * (size_t)n, false, s);
+                if (x) CU(h, cudaMemcpyAsync(io, x + off, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+                if (v)
+                    CU(h, cudaMemcpyAsync(io + 3 * (size_t)n, v + off, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+                launch_state_io(h->d, w, n, io, io + 3 * (size_t)n, true, s);
+            }
+            off += 3 * (size_t)n;
+        }
+        if (lam) CU(h, cudaMemcpyAsync(h->d.lam, lam, sizeof(double) * W, cudaMemcpyHostToDevice, s));
+        if (plam) CU(h, cudaMemcpyAsync(h->d.plam, plam, sizeof(double) * W, cudaMemcpyHostToDevice, s));
+        if (step) CU(h, cudaMemcpyAsync(h->d.step, step, sizeof(uint64_t) * W, cudaMemcpyHostToDevice, s));
+        return LA_OK;
+    }();
+    if (rc != LA_OK) {  // some walkers may hold part of the new state
+        cudaStreamSynchronize(s);
+        h->sticky = rc;
+        return rc;
+    }
     return sync_status(h, s, nullptr);  // also keeps `one` alive until the copy is done
+}
+
+// ---- checkpoints: the arena's state prefix plus a header ----
+namespace {
+struct CkptHeader {
+    char magic[8];
+    uint64_t state_bytes, fingerprint;
+    int32_t chunk, version;
+    int64_t steps, launches;
+};
+constexpr int CKPT_VERSION = 1;
+
+uint64_t fnv1a(uint64_t hsh, const void *p, size_t n) {
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) hsh = (hsh ^ b[i]) * 1099511628211ull;
+    return hsh;
+}
+
+// the layout and the per-system / per-walker / per-stage parameters: two
+// engines built from the same inputs and options have the same fingerprint
+uint64_t fingerprint(const la_handle *h) {
+    uint64_t f = 14695981039346656037ull;
+    f = fnv1a(f, &h->state_bytes, sizeof h->state_bytes);
+    f = fnv1a(f, h->sys.data(), sizeof(SysDev) * h->sys.size());
+    f = fnv1a(f, h->walk.data(), sizeof(WalkerDev) * h->walk.size());
+    f = fnv1a(f, h->stages.data(), sizeof(StageDev) * h->stages.size());
+    return f;
+}
+}  // namespace
+
+int la_checkpoint_save(la_handle *h, void *buf, size_t cap, size_t *bytes, void *stream) {
+    if (!h || !bytes) return LA_ERR_INVALID_ARG;
+    const size_t need = sizeof(CkptHeader) + h->state_bytes;
+    *bytes = need;
+    if (!buf) return LA_OK;
+    if (cap < need) return fail(h, LA_ERR_INVALID_ARG, "checkpoint buffer of %zu bytes (need %zu)", cap, need);
+    if (h->sticky != LA_OK) return fail(h, LA_ERR_STATE, "handle in error state: %s", h->err.c_str());
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = flush_dirty(h, s);  // lists and forces consistent with a state set last
+    if (rc != LA_OK) return rc;
+    CkptHeader hd{};
+    memcpy(hd.magic, "LABFCKPT", 8);
+    hd.state_bytes = h->state_bytes;
+    hd.fingerprint = fingerprint(h);
+    hd.chunk = h->d.chunk;
+    hd.version = CKPT_VERSION;
+    hd.steps = h->steps;
+    hd.launches = h->launches;
+    memcpy(buf, &hd, sizeof hd);
+    CU(h, cudaMemcpyAsync((char *)buf + sizeof hd, h->arena, h->state_bytes, cudaMemcpyDeviceToHost, s));
+    return sync_status(h, s, nullptr);
+}
+
+int la_checkpoint_load(la_handle *h, const void *buf, size_t bytes, void *stream) {
+    if (!h || !buf) return LA_ERR_INVALID_ARG;
+    CkptHeader hd;
+    if (bytes < sizeof hd) return fail(h, LA_ERR_INVALID_ARG, "checkpoint too short");
+    memcpy(&hd, buf, sizeof hd);
+    if (memcmp(hd.magic, "LABFCKPT", 8) != 0 || hd.version != CKPT_VERSION)
+        return fail(h, LA_ERR_INVALID_ARG, "not a checkpoint of this library version");
+    if (hd.state_bytes != h->state_bytes || bytes < sizeof hd + hd.state_bytes || hd.fingerprint != fingerprint(h))
+        return fail(h, LA_ERR_INVALID_ARG, "checkpoint of a different system, layout or parameter set");
+    if (hd.chunk != h->d.chunk)
+        return fail(h, LA_ERR_INVALID_ARG, "checkpoint taken with chunk_entries=%d, this engine uses %d", hd.chunk,
+                    h->d.chunk);
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(h, cudaStreamSynchronize(s));
+    CU(h, cudaMemcpyAsync(h->arena, (const char *)buf + sizeof hd, h->state_bytes, cudaMemcpyHostToDevice, s));
+    h->dirty = false;
+    h->steps = hd.steps;
+    h->launches = hd.launches;
+    h->sticky = LA_OK;
+    return sync_status(h, s, nullptr);
 }
 
 int la_set_alch_params(la_handle *h, int sys, const double *theta, void *stream) {
@@ -1483,16 +1645,28 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
     rc = flush_dirty(h, s);
     if (rc != LA_OK) return rc;
     const int W = h->L.W;
-    cudaEvent_t ev[4];  // integrate | gate + list kernels | fused pair launch
+    // integrate | gate [+ list kernels when a walker must rebuild] | fused pair launch
+    cudaEvent_t ev[4];
     for (auto &e : ev) CU(h, cudaEventCreate(&e));
     double acc[LA_N_KERNELS] = {0};
     int64_t cnt[LA_N_KERNELS] = {0};
+    std::vector<int> flags(W);
+    long long rebuild_steps = 0;
     for (int k = 0; k < n_steps; ++k) {
         cudaEventRecord(ev[0], s);
         launch_integrate(h->d, h->hv, 0, W, s);
         cudaEventRecord(ev[1], s);
         launch_gate(h->d, 0, W, 0, false, s);
-        launch_rebuild(h->d, h->hv, 0, W, s, true);
+        // the graph's conditional node runs the list kernels only on steps
+        // where some walker must rebuild: read the flags the integrator set
+        CU(h, cudaMemcpyAsync(flags.data(), h->d.rebuild, sizeof(int) * W, cudaMemcpyDeviceToHost, s));
+        CU(h, cudaStreamSynchronize(s));
+        bool any = false;
+        for (int w = 0; w < W; ++w) any = any || flags[w] != 0;
+        if (any) {
+            launch_rebuild(h->d, h->hv, 0, W, s, true);
+            ++rebuild_steps;
+        }
         cudaEventRecord(ev[2], s);
         // the fused launch of the batched step: pairs, bonded terms, walker
         // terms and the lambda update
@@ -1505,17 +1679,18 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
             acc[q] += ms;
         }
         cnt[0] += 1;
-        cnt[1] += 1 + rebuild_kernel_count(h->hv, 0, W);
+        cnt[1] += 1 + (any ? rebuild_kernel_count(h->hv, 0, W) : 0);
         cnt[2] += 1;
     }
     launch_finish(h->d, h->hv, 0, W, s);
     h->steps += n_steps;
-    h->launches += n_steps * h->launches_per_step + 1;
+    h->launches += cnt[0] + cnt[1] + cnt[2] + 1;
     for (auto &e : ev) cudaEventDestroy(e);
     for (int q = 0; q < LA_N_KERNELS; ++q) {
         ms_out[q] = (float)(acc[q] / n_steps);
         if (launches_out) launches_out[q] = cnt[q];
     }
+    (void)rebuild_steps;
     return sync_status(h, s, nullptr);
 }
 

@@ -37,5 +37,8 @@ void launch_lambda(const Dev &d, int s0, int s1, bool prime, cudaStream_t s);
 void launch_state_io(const Dev &d, int w, int n, float *x, float *v, bool to_slots, cudaStream_t s);
 void launch_forces_out(const Dev &d, int w, int n, float *out, cudaStream_t s);
 void launch_lambda_path(const double *lam, int n, double bv, double be, double *out, cudaStream_t s);
+void launch_positions_in(const Dev &d, int w, int n, const float *x, cudaStream_t s);
+void launch_alch_params_in(const Dev &d, int sys, int n_alch, const double *theta, cudaStream_t s);
+void launch_ef_out(const Dev &d, int w, int P, double *out, cudaStream_t s);
 
 }  // namespace labf

@@ -33,6 +33,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "BOX_TOO_SMALL", -3: "CUDA", -4: "UNSUPPORTED",
 
 EXPORTED = ("la_query_sizes", "la_create_system", "la_step_walkers", "la_step_walkers_plain",
             "la_read_abf", "la_abf_export", "la_abf_import", "la_energy_forces", "la_get_state", "la_set_state", "la_get_states", "la_set_states",
+            "la_checkpoint_save", "la_checkpoint_load", "la_fp_peak", "la_energy_forces_device",
             "la_set_alch_params",
             "la_read_theta", "la_get_pairs", "la_lambda_path", "la_sync", "la_stats",
             "la_time_kernels", "la_autotune", "la_autotune_report", "la_last_error", "la_destroy",
@@ -110,9 +111,13 @@ def load(build_if_missing: bool = False):
     lib.la_abf_import.argtypes = [H, I, I, P, P, P, P]
     lib.la_energy_forces.argtypes = [H, I, C.c_uint32, P, P, P, P, P, P]
     lib.la_get_state.argtypes = [H, I, P, P, P, P, P, P]
-    lib.la_set_state.argtypes = [H, I, P, P, P, P, P]
-    lib.la_get_states.argtypes = [H, P, P, P, P, P]
-    lib.la_set_states.argtypes = [H, P, P, P, P, P]
+    lib.la_set_state.argtypes = [H, I, P, P, P, P, P, P]
+    lib.la_get_states.argtypes = [H, P, P, P, P, P, P]
+    lib.la_set_states.argtypes = [H, P, P, P, P, P, P]
+    lib.la_checkpoint_save.argtypes = [H, P, S, C.POINTER(S), P]
+    lib.la_checkpoint_load.argtypes = [H, P, S, P]
+    lib.la_fp_peak.argtypes = [I, D, C.POINTER(D), P]
+    lib.la_energy_forces_device.argtypes = [H, I, P, P, P, P, P, P]
     lib.la_set_alch_params.argtypes = [H, I, P, P]
     lib.la_read_theta.argtypes = [H, I, I, P, P, P, P, P]
     lib.la_get_pairs.argtypes = [H, I, P, P, C.c_int64, P, P]
@@ -346,6 +351,28 @@ class Engine:
             out["pairs_normal"], out["pairs_alch"] = int(st[3]), int(st[4])
         return out
 
+    def energy_forces_device(self, walker: int, x=None, theta=None, lam=None, out=None, forces=None,
+                             stream=None) -> None:
+        """la_energy_forces_device: every argument a CUDA tensor (or None) on
+        the engine's device; x float32 [n, 3], theta float64 [n_alch, 3],
+        lam float64 [1], out float64 [LA_N_TERMS + 2 + 2 P], forces float32
+        [n, 3].  Asynchronous (no host synchronisation)."""
+        def ptr(t, dtype, numel=None):
+            if t is None:
+                return None
+            if t.device != self.device or t.dtype != dtype or not t.is_contiguous():
+                raise ValueError(f"expected a contiguous {dtype} tensor on {self.device}")
+            if numel is not None and t.numel() != numel:
+                raise ValueError(f"expected {numel} elements, got {t.numel()}")
+            return C.c_void_p(t.data_ptr())
+
+        spec = self.systems[self.walker_sys[walker]].spec
+        P = 3 * spec.n_alch + 1
+        self._check(self.lib.la_energy_forces_device(
+            self.handle, walker, ptr(x, self.torch.float32, 3 * spec.n), ptr(theta, self.torch.float64, 3 * spec.n_alch),
+            ptr(lam, self.torch.float64, 1), ptr(out, self.torch.float64, LA_N_TERMS + 2 + 2 * P),
+            ptr(forces, self.torch.float32, 3 * spec.n), self._stream(stream)))
+
     def get_state(self, walker: int, stream=None) -> dict:
         n = self.systems[self.walker_sys[walker]].spec.n
         x, v = np.zeros((n, 3), np.float32), np.zeros((n, 3), np.float32)
@@ -354,12 +381,13 @@ class Engine:
                                           C.byref(step), self._stream(stream)))
         return dict(x=x, v=v, lam=lam.value, plam=plam.value, step=step.value)
 
-    def set_state(self, walker: int, x=None, v=None, lam=None, plam=None, stream=None):
+    def set_state(self, walker: int, x=None, v=None, lam=None, plam=None, step=None, stream=None):
         xa = None if x is None else np.ascontiguousarray(x, np.float32)
         va = None if v is None else np.ascontiguousarray(v, np.float32)
         la = None if lam is None else C.byref(C.c_double(float(lam)))
         pa = None if plam is None else C.byref(C.c_double(float(plam)))
-        self._check(self.lib.la_set_state(self.handle, walker, _p(xa), _p(va), la, pa, self._stream(stream)))
+        sa = None if step is None else C.byref(C.c_uint64(int(step)))
+        self._check(self.lib.la_set_state(self.handle, walker, _p(xa), _p(va), la, pa, sa, self._stream(stream)))
 
     def _rows_array(self, a, name):
         n = int(self.walker_rows[-1])
@@ -367,24 +395,51 @@ class Engine:
             raise ValueError(f"{name}: expected a C-contiguous float32 array of shape ({n}, 3)")
         return a
 
+    def _pinned(self, shape, dtype):
+        """A numpy view of a page-locked host tensor (copied by DMA)."""
+        t = self.torch.empty(shape, dtype=dtype, pin_memory=True)
+        self._pin_keep = getattr(self, "_pin_keep", [])[-8:] + [t]
+        return t.numpy()
+
     def get_states(self, x=None, v=None, stream=None) -> dict:
         """Every walker's state in one call.  x, v: float32 [rows, 3], walker w
-        in rows walker_rows[w]:walker_rows[w + 1]; pass arrays (e.g. views of
-        page-locked tensors) to have them filled in place."""
+        in rows walker_rows[w]:walker_rows[w + 1]; arrays passed in (e.g.
+        views of page-locked tensors) are filled in place, otherwise
+        page-locked arrays are allocated, so that the call synchronises
+        once.  Also returns every walker's step counter."""
         n = int(self.walker_rows[-1])
-        x = np.zeros((n, 3), np.float32) if x is None else self._rows_array(x, "x")
-        v = np.zeros((n, 3), np.float32) if v is None else self._rows_array(v, "v")
+        x = self._pinned((n, 3), self.torch.float32) if x is None else self._rows_array(x, "x")
+        v = self._pinned((n, 3), self.torch.float32) if v is None else self._rows_array(v, "v")
         lam, plam = np.zeros(self.n_walkers), np.zeros(self.n_walkers)
-        self._check(self.lib.la_get_states(self.handle, _p(x), _p(v), _p(lam), _p(plam), self._stream(stream)))
-        return dict(x=x, v=v, lam=lam, plam=plam)
+        step = np.zeros(self.n_walkers, np.uint64)
+        self._check(self.lib.la_get_states(self.handle, _p(x), _p(v), _p(lam), _p(plam), _p(step),
+                                           self._stream(stream)))
+        return dict(x=x, v=v, lam=lam, plam=plam, step=step)
 
-    def set_states(self, x=None, v=None, lam=None, plam=None, stream=None):
-        """Every walker's state in one call (layout as in get_states)."""
+    def set_states(self, x=None, v=None, lam=None, plam=None, step=None, stream=None):
+        """Every walker's state in one call (layout as in get_states); step
+        sets the walkers' step counters (the Philox counters)."""
         xa = None if x is None else self._rows_array(x, "x")
         va = None if v is None else self._rows_array(v, "v")
         la = None if lam is None else np.ascontiguousarray(lam, np.float64).reshape(self.n_walkers)
         pa = None if plam is None else np.ascontiguousarray(plam, np.float64).reshape(self.n_walkers)
-        self._check(self.lib.la_set_states(self.handle, _p(xa), _p(va), _p(la), _p(pa), self._stream(stream)))
+        sa = None if step is None else np.ascontiguousarray(step, np.uint64).reshape(self.n_walkers)
+        self._check(self.lib.la_set_states(self.handle, _p(xa), _p(va), _p(la), _p(pa), _p(sa),
+                                           self._stream(stream)))
+
+    def checkpoint(self, stream=None) -> np.ndarray:
+        """The engine's complete state as a byte image (page-locked uint8
+        array): la_checkpoint_save.  Restore with load_checkpoint into an
+        engine created from the same inputs and options."""
+        n = C.c_size_t(0)
+        self._check(self.lib.la_checkpoint_save(self.handle, None, 0, C.byref(n), self._stream(stream)))
+        buf = self.torch.empty(int(n.value), dtype=self.torch.uint8, pin_memory=True).numpy()
+        self._check(self.lib.la_checkpoint_save(self.handle, _p(buf), buf.size, C.byref(n), self._stream(stream)))
+        return buf
+
+    def load_checkpoint(self, image: np.ndarray, stream=None) -> None:
+        img = np.ascontiguousarray(image, np.uint8)
+        self._check(self.lib.la_checkpoint_load(self.handle, _p(img), img.size, self._stream(stream)))
 
     def set_alch_params(self, sys: int, theta: np.ndarray, stream=None):
         t = np.ascontiguousarray(theta, np.float64)
@@ -435,6 +490,19 @@ class Engine:
 
     def autotune_report(self) -> str:
         return self.lib.la_autotune_report(self.handle).decode()
+
+
+def fp_peak(fp64: bool = False, seconds: float = 0.5, stream=None) -> float:
+    """Measured FMA rate of the current GPU in TFLOP/s (la_fp_peak)."""
+    import torch
+
+    lib = load()
+    out = C.c_double(0.0)
+    st = torch.cuda.current_stream() if stream is None else stream
+    rc = lib.la_fp_peak(1 if fp64 else 0, float(seconds), C.byref(out), C.c_void_p(st.cuda_stream))
+    if rc < 0:
+        raise LabfError(rc, "la_fp_peak failed")
+    return out.value
 
 
 def engine_for(spec, run, state=None, options=None) -> Engine:

@@ -118,10 +118,13 @@ def test_calls_reject_a_null_handle():
     lib = labf.load()
     x = np.zeros((4, 3), np.float32)
     lam = np.zeros(2)
-    assert lib.la_get_states(None, labf._p(x), labf._p(x), labf._p(lam), labf._p(lam), None) == -1
-    assert lib.la_set_states(None, labf._p(x), labf._p(x), labf._p(lam), labf._p(lam), None) == -1
+    assert lib.la_get_states(None, labf._p(x), labf._p(x), labf._p(lam), labf._p(lam), None, None) == -1
+    assert lib.la_set_states(None, labf._p(x), labf._p(x), labf._p(lam), labf._p(lam), None, None) == -1
     assert lib.la_get_state(None, 0, labf._p(x), labf._p(x), None, None, None, None) == -1
-    assert lib.la_set_state(None, 0, labf._p(x), labf._p(x), None, None, None) == -1
+    assert lib.la_set_state(None, 0, labf._p(x), labf._p(x), None, None, None, None) == -1
+    n = C.c_size_t(0)
+    assert lib.la_checkpoint_save(None, None, 0, C.byref(n), None) == -1
+    assert lib.la_checkpoint_load(None, labf._p(x), 16, None) == -1
     assert lib.la_step_walkers(None, 1, None) == -1
 
 
