@@ -205,6 +205,121 @@ def flush_l2(buf):
     buf.add_(1)  # 256 MB read + write, larger than the 129 MB L2
 
 
+def _timed_steps(eng, md_steps, stream, plain=False):
+    """Device milliseconds of md_steps MD steps (CUDA events on the stream)."""
+    import torch
+
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    (eng.step_plain if plain else eng.step)(md_steps, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def _count_pairs(eng):
+    n = a = 0
+    for w in range(eng.n_walkers):
+        r = eng.energy_forces(w, count_pairs=True, forces=False)
+        n += r["pairs_normal"]
+        a += r["pairs_alch"]
+    return n, a
+
+
+def bench_uneven(args, stream, peak_tflops):
+    """Batched uneven systems: 64 walkers over 8 water boxes of 256 ... 8192
+    waters (4 ... 40-site solutes), one graph, autotuned, against one launch
+    sequence per walker without graphs on the same GPU."""
+    from paper_2307_08006_gb300 import labf, synth
+
+    inputs = []
+    for k, sp in enumerate(synth.uneven_batch(8008)):
+        rng = np.random.default_rng(8008 + k)
+        sp.x = ((sp.x + rng.normal(0.0, 0.01, sp.x.shape)) % sp.box).astype(np.float32)
+        run = synth.uneven_run(seed=8008 + k, walkers_per_system=8)
+        inputs.append(labf.SystemInput(sp, run, synth.initial_state(sp, run)))
+    t0 = time.perf_counter()
+    eng = labf.Engine(inputs, options=dict(graph_steps=args.graph_steps, autotune=1, prune_margin=args.prune_margin))
+    eng.step(args.settle // 2)
+    eng.sync()
+    eng.autotune()
+    setup_s = time.perf_counter() - t0
+    pn, pa = _count_pairs(eng)
+    W = eng.n_walkers
+    atoms = sum(si.spec.n * si.run.n_walkers for si in inputs)
+    dt = inputs[0].run.dt
+    md = args.md_steps
+    _timed_steps(eng, md, stream)  # warm-up
+    ms = sum(_timed_steps(eng, md, stream) for _ in range(3)) / 3.0
+    plain_md = max(5, md // 20)
+    _timed_steps(eng, 2, stream, plain=True)
+    pms = _timed_steps(eng, plain_md, stream, plain=True)
+    kt = eng.time_kernels(args.profile_steps, stream)
+    st = eng.stats()
+    out = dict(
+        workload="batched uneven systems: 8 water boxes (256, 512, 1024, 2048, 3072, 4096, 6144, 8192 waters; "
+                 "4-40-site alchemical solutes; r_c 1.0 nm, 0.85 nm for the 1.98 nm box; list skin 0.1 nm, "
+                 f"pruning margin {args.prune_margin:g} nm), 8 walkers each (64), one CUDA graph, autotuned",
+        walkers=W, atoms_all_walkers=atoms, md_steps=3 * md,
+        value=walker_ns_per_day(W, md, dt, ms * 1e-3), unit=UNIT, ms_per_md_step=ms / md,
+        pair_interactions_per_s=(pn + pa) * md / (ms * 1e-3), in_cutoff_pairs_per_md_step=pn + pa,
+        plain_form=dict(value=walker_ns_per_day(W, plain_md, dt, pms * 1e-3), unit=UNIT, md_steps=plain_md,
+                        ms_per_md_step=pms / plain_md, note="one walker per launch sequence, no CUDA graph"),
+        batched_over_plain=(pms / plain_md) / (ms / md),
+        lists=dict(tiles_8x4=int(st[6]), cluster_pair_entries=int(st[5]),
+                   tile_efficiency=pn / max(1, 32 * int(st[6]))),
+        kernel_ms=dict((k, v[0]) for k, v in kt.items()),
+        launch=eng.autotune_report(), setup_s=setup_s)
+    pair_ms = kt["pairs"][0]
+    ach = (pn + pa) * FLOP_PER_PAIR / (pair_ms * 1e-3) / 1e12
+    out["roofline"] = dict(bound="alu", achieved=ach, peak=peak_tflops, unit="TFLOP/s", frac=ach / peak_tflops,
+                           pair_kernel_ms=pair_ms)
+    eng.close()
+    return out
+
+
+def bench_large(args, stream, peak_tflops):
+    """Large synthetic complex: 31 000 waters + a 3000-site restrained chain +
+    a 40-site alchemical ligand with a flat-bottom restraint (96 040 atoms,
+    r_c 1.2 nm), 16 walkers."""
+    from paper_2307_08006_gb300 import labf, synth
+
+    sp = synth.large_complex()
+    run = synth.large_complex_run()
+    t0 = time.perf_counter()
+    eng = labf.Engine([labf.SystemInput(sp, run, synth.initial_state(sp, run))],
+                      options=dict(graph_steps=args.graph_steps, autotune=1, prune_margin=args.prune_margin))
+    eng.step(args.settle // 4)
+    eng.sync()
+    eng.autotune()
+    setup_s = time.perf_counter() - t0
+    pn, pa = _count_pairs(eng)
+    W = eng.n_walkers
+    md = max(20, args.md_steps // 2)
+    _timed_steps(eng, md, stream)
+    ms = sum(_timed_steps(eng, md, stream) for _ in range(3)) / 3.0
+    kt = eng.time_kernels(max(5, args.profile_steps // 2), stream)
+    st = eng.stats()
+    pair_ms = kt["pairs"][0]
+    ach = (pn + pa) * FLOP_PER_PAIR / (pair_ms * 1e-3) / 1e12
+    out = dict(
+        workload="large synthetic complex: 31000 flexible waters + 3000-site chain (0.15 nm bonds, positional "
+                 "restraints) + 40-site alchemical ligand (flat-bottom restraint to the chain), 96040 atoms, "
+                 f"9.92 nm box, r_c 1.2 nm, list skin 0.1 nm, pruning margin {args.prune_margin:g} nm",
+        walkers=W, atoms_per_walker=sp.n, md_steps=3 * md,
+        value=walker_ns_per_day(W, md, run.dt, ms * 1e-3), unit=UNIT, ms_per_md_step=ms / md,
+        pair_interactions_per_s=(pn + pa) * md / (ms * 1e-3), in_cutoff_pairs_per_md_step=pn + pa,
+        lists=dict(tiles_8x4=int(st[6]), cluster_pair_entries=int(st[5]),
+                   tile_efficiency=pn / max(1, 32 * int(st[6]))),
+        kernel_ms=dict((k, v[0]) for k, v in kt.items()),
+        roofline=dict(bound="alu", achieved=ach, peak=peak_tflops, unit="TFLOP/s", frac=ach / peak_tflops,
+                      pair_kernel_ms=pair_ms,
+                      kernel="k_pairs, fused step launch (normal + alchemical pairs, bonded, walker, lambda)"),
+        launch=eng.autotune_report(), setup_s=setup_s)
+    eng.close()
+    return out
+
+
 def gpu_arm(args):
     import torch
 
@@ -307,7 +422,7 @@ def gpu_arm(args):
         st = eng.get_states(x=px, v=pv)
         lam[:], plam[:] = st["lam"], st["plam"]
 
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = max(2, args.steps)
     e2e_step()
     flush_l2(flush)
     torch.cuda.synchronize()
@@ -343,6 +458,21 @@ def gpu_arm(args):
     achieved = pairs_per_md * FLOP_PER_PAIR / (pair_ms * 1e-3) / 1e12
     eng.sync()
     csum = clk.summary(local)
+    # measured FMA peaks (FP32 and FP64), clocks sampled during them
+    peaks = None
+    if not args.no_peaks:
+        clk2 = ClockSampler(os.path.join(args.out_dir, f"clocks_peaks_rank{rank}.csv"))
+        with clk2:
+            fp32 = labf.fp_peak(False, 1.0, stream)
+            fp64 = labf.fp_peak(True, 0.5, stream)
+        peaks = dict(fp32_tflops=fp32, fp64_tflops=fp64, nominal_fp32_tflops=peak_tflops,
+                     clocks=clk2.summary(local),
+                     note="la_fp_peak: independent FMA chains on every SM, CUDA events, about 1 s (FP32) "
+                          "and 0.5 s (FP64) of device time")
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra["C3"] = bench_uneven(args, stream, peak_tflops)
+        extra["C5"] = bench_large(args, stream, peak_tflops)
     # the integrator streams per atom: F (24 B), 1/m and noise scale (8),
     # v (16), x (16), reference x (16), slot indices (8) read; x, v (32) and
     # the cleared F (24) written
@@ -385,12 +515,19 @@ def gpu_arm(args):
                           frac=achieved / peak_tflops, traffic=traffic, traffic_source=traffic_src,
                           kernel="k_pairs, fused step launch (normal + alchemical pairs, bonded, walker, lambda)",
                           pair_kernel_ms=pair_ms,
-                          peak_note=f"{n_sm} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+                          peak_note=f"{n_sm} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock), nominal",
+                          peak_measured=peaks["fp32_tflops"] if peaks else None,
+                          frac_of_measured=achieved / peaks["fp32_tflops"] if peaks else None,
+                          flop_per_pair=FLOP_PER_PAIR,
                           kernel_ms=dict((k, v[0]) for k, v in kt.items()),
+                          kernel_ms_sum=sum(v[0] for v in kt.values()),
+                          md_step_ms=ms / args.steps / md,
                           timing_note="CUDA events on the engine stream between the launches of the batched "
-                                      "step (integrate | gate + list kernels | fused pair launch with bonded, "
-                                      "walker and lambda work) over --profile-steps steps, right after the timed "
-                                      "region (kernel nodes of the graph cannot be timed one by one)"),
+                                      "step as the graph runs them (integrate | gate, and the list kernels on "
+                                      "steps where a walker rebuilds | fused pair launch with bonded, walker and "
+                                      "lambda work) over --profile-steps steps right after the timed region; "
+                                      "kernel_ms_sum against md_step_ms (the graph-timed MD step) leaves the "
+                                      "launch gaps"),
             roofline_hbm=dict(bound="hbm", kernel="k_integrate", achieved=integ_gbs, peak=hbm_peak,
                               unit="GB/s", frac=integ_gbs / hbm_peak, bytes_per_launch=integ_bytes,
                               peak_source=hbm_src),
@@ -399,6 +536,9 @@ def gpu_arm(args):
         )
         if cb is not None:
             line["cpu_baseline"] = cb
+        if peaks is not None:
+            line["peaks"] = peaks
+        line.update(extra)
         print(json.dumps(line))
     eng.close()
     if dist is not None:
@@ -419,6 +559,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and large-complex workloads")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FP32/FP64 FMA peak measurement")
     ap.add_argument("--launch", default="",
                     help="fixed pair-kernel shape, e.g. pair_variant=1,pair_ctas_per_sm=6,chunk_entries=64")
     ap.add_argument("--skin", type=float, default=SKIN_NM, help="list skin (nm)")

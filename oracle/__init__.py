@@ -116,6 +116,8 @@ def _declare(lib):
     lib.or_list_threshold.restype = C.c_int64
     lib.or_pair_set.argtypes = [C.POINTER(_System), P, C.c_double, C.c_int64, P, P, C.c_int64]
     lib.or_pair_set.restype = C.c_int64
+    lib.or_pair_set_rows.argtypes = [C.POINTER(_System), P, C.c_double, C.c_int64, P, P, P, C.c_int64]
+    lib.or_pair_set_rows.restype = C.c_int64
     lib.or_energy_forces.argtypes = [C.POINTER(_System), P, C.c_double, P, P, P, P, P, P]
     lib.or_energy_forces_masked.argtypes = [C.POINTER(_System), P, C.c_double, P, P, P, P, P, P, P]
     lib.or_set_threads.argtypes = [C.c_int]
@@ -234,6 +236,22 @@ def pair_set(osys: OracleSystem, x: np.ndarray, r_list: float):
     pairs = np.zeros((max(cnt, 1), 2), np.int32)
     kind = np.zeros(max(cnt, 1), np.uint8)
     lib.or_pair_set(C.byref(osys.c), _ptr(x), box_inv, R, _ptr(pairs), _ptr(kind), cnt)
+    return pairs[:cnt], kind[:cnt]
+
+
+def pair_set_rows(osys: OracleSystem, x: np.ndarray, r_list: float, atoms):
+    """The pairs of pair_set that involve at least one of `atoms` (same
+    definition and order), for checking very large systems on a sample."""
+    x = np.ascontiguousarray(x, np.float32)
+    box_inv = 1.0 / osys.spec.box
+    R = list_threshold(r_list, box_inv)
+    rows = np.zeros(osys.spec.n, np.uint8)
+    rows[np.asarray(atoms)] = 1
+    lib = _load()
+    cnt = lib.or_pair_set_rows(C.byref(osys.c), _ptr(x), box_inv, R, _ptr(rows), None, None, 0)
+    pairs = np.zeros((max(cnt, 1), 2), np.int32)
+    kind = np.zeros(max(cnt, 1), np.uint8)
+    lib.or_pair_set_rows(C.byref(osys.c), _ptr(x), box_inv, R, _ptr(rows), _ptr(pairs), _ptr(kind), cnt)
     return pairs[:cnt], kind[:cnt]
 
 

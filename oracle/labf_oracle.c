@@ -198,6 +198,38 @@ int64_t or_pair_set(const or_system *sys, const float *x, double box_inv, int64_
     return cnt;
 }
 
+/* The pairs of or_pair_set that involve at least one atom flagged in
+ * rows[n] (the same definition, visited only for flagged atoms, so that
+ * very large systems can be checked on a sample of atoms).  Output in the
+ * same (i, j) order as or_pair_set. */
+int64_t or_pair_set_rows(const or_system *sys, const float *x, double box_inv, int64_t R, const uint8_t *rows,
+                         int32_t *pairs, uint8_t *kind, int64_t cap) {
+    int n = sys->n;
+    uint32_t *u = (uint32_t *)malloc(sizeof(uint32_t) * 3 * (size_t)n);
+    or_quantize(n, x, box_inv, u);
+    int64_t cnt = 0;
+    for (int i = 0; i < n; ++i) {
+        for (int j = i + 1; j < n; ++j) {
+            if (!rows[i] && !rows[j]) continue;
+            if (or_excluded(sys, i, j)) continue;
+            int64_t dx = torus_delta(u[3 * i], u[3 * j]);
+            int64_t dy = torus_delta(u[3 * i + 1], u[3 * j + 1]);
+            int64_t dz = torus_delta(u[3 * i + 2], u[3 * j + 2]);
+            int64_t D = dx * dx + dy * dy + dz * dz;
+            if (D < R) {
+                if (cnt < cap) {
+                    pairs[2 * cnt] = i;
+                    pairs[2 * cnt + 1] = j;
+                    kind[cnt] = (uint8_t)((sys->alch[i] ? 1 : 0) + (sys->alch[j] ? 1 : 0));
+                }
+                ++cnt;
+            }
+        }
+    }
+    free(u);
+    return cnt;
+}
+
 /* ------------------------------------------------------------------ */
 /* Energies, forces, dU/dlambda, dU/dtheta                              */
 /* ------------------------------------------------------------------ */

@@ -93,6 +93,8 @@ void or_quantize(int n, const float *x, double box_inv, uint32_t *u);
 int64_t or_list_threshold(double r_list, double box_inv);
 int64_t or_pair_set(const or_system *sys, const float *x, double box_inv, int64_t R,
                     int32_t *pairs, uint8_t *kind, int64_t cap);
+int64_t or_pair_set_rows(const or_system *sys, const float *x, double box_inv, int64_t R, const uint8_t *rows,
+                         int32_t *pairs, uint8_t *kind, int64_t cap);
 
 void or_energy_forces(const or_system *sys, const double *x, double lam,
                       double terms[OR_N_TERMS], double *F, double dl[3], double *dUdl,

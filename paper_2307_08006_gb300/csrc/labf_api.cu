@@ -1645,39 +1645,41 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
     rc = flush_dirty(h, s);
     if (rc != LA_OK) return rc;
     const int W = h->L.W;
-    // integrate | gate [+ list kernels when a walker must rebuild] | fused pair launch
-    cudaEvent_t ev[4];
+    // integrate | gate | (host reads the flags) | list kernels when a walker
+    // must rebuild | fused pair launch; the host's gap is in no class
+    cudaEvent_t ev[6];
     for (auto &e : ev) CU(h, cudaEventCreate(&e));
     double acc[LA_N_KERNELS] = {0};
     int64_t cnt[LA_N_KERNELS] = {0};
     std::vector<int> flags(W);
-    long long rebuild_steps = 0;
     for (int k = 0; k < n_steps; ++k) {
         cudaEventRecord(ev[0], s);
         launch_integrate(h->d, h->hv, 0, W, s);
         cudaEventRecord(ev[1], s);
         launch_gate(h->d, 0, W, 0, false, s);
+        cudaEventRecord(ev[2], s);
         // the graph's conditional node runs the list kernels only on steps
         // where some walker must rebuild: read the flags the integrator set
         CU(h, cudaMemcpyAsync(flags.data(), h->d.rebuild, sizeof(int) * W, cudaMemcpyDeviceToHost, s));
         CU(h, cudaStreamSynchronize(s));
         bool any = false;
         for (int w = 0; w < W; ++w) any = any || flags[w] != 0;
-        if (any) {
-            launch_rebuild(h->d, h->hv, 0, W, s, true);
-            ++rebuild_steps;
-        }
-        cudaEventRecord(ev[2], s);
+        cudaEventRecord(ev[3], s);
+        if (any) launch_rebuild(h->d, h->hv, 0, W, s, true);
+        cudaEventRecord(ev[4], s);
         // the fused launch of the batched step: pairs, bonded terms, walker
         // terms and the lambda update
         launch_pairs_fused(h->d, h->hv, (int)h->stages.size(), s);
-        cudaEventRecord(ev[3], s);
-        CU(h, cudaEventSynchronize(ev[3]));
-        for (int q = 0; q < 3; ++q) {  // bonded, walker, lambda run inside the pair launch: 0
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
-            acc[q] += ms;
-        }
+        cudaEventRecord(ev[5], s);
+        CU(h, cudaEventSynchronize(ev[5]));
+        float t01 = 0.f, t12 = 0.f, t34 = 0.f, t45 = 0.f;
+        cudaEventElapsedTime(&t01, ev[0], ev[1]);
+        cudaEventElapsedTime(&t12, ev[1], ev[2]);
+        cudaEventElapsedTime(&t34, ev[3], ev[4]);
+        cudaEventElapsedTime(&t45, ev[4], ev[5]);
+        acc[0] += t01;
+        acc[1] += t12 + (any ? t34 : 0.f);
+        acc[2] += t45;  // bonded, walker, lambda run inside the pair launch: 0
         cnt[0] += 1;
         cnt[1] += 1 + (any ? rebuild_kernel_count(h->hv, 0, W) : 0);
         cnt[2] += 1;
@@ -1690,7 +1692,6 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
         ms_out[q] = (float)(acc[q] / n_steps);
         if (launches_out) launches_out[q] = cnt[q];
     }
-    (void)rebuild_steps;
     return sync_status(h, s, nullptr);
 }
 

@@ -679,3 +679,22 @@ def test_lambda_dependent_restraint_endpoints():
     assert mid["dUdl"] == pytest.approx(0.0, abs=1e-9)  # d_min is stationary at 1/2
     q = oracle.energy_forces(o, x, 0.25)  # d_min = delta/2, slope delta pi
     assert q["dl"][2] == pytest.approx(-k * (ra - 0.5 * delta) * delta * np.pi, rel=1e-12)
+
+
+def test_pair_set_rows_is_the_pair_set_restricted_to_the_rows():
+    """or_pair_set_rows returns exactly the pairs of the brute-force set
+    (and of or_pair_set) touching a selected atom, in the same order."""
+    sp, x = _small_water(5)
+    x = x.astype(np.float32)
+    o = oracle.OracleSystem(sp)
+    full, fkind = oracle.pair_set(o, x, 1.0)
+    brute = _brute_pairs(sp, x, 1.0)
+    rng = np.random.default_rng(3)
+    for k in (1, 7, sp.n // 2, sp.n):
+        rows = np.sort(rng.choice(sp.n, k, replace=False))
+        sel = np.zeros(sp.n, bool)
+        sel[rows] = True
+        got, kind = oracle.pair_set_rows(o, x, 1.0, rows)
+        keep = sel[full[:, 0]] | sel[full[:, 1]]
+        assert np.array_equal(got, full[keep]) and np.array_equal(kind, fkind[keep])
+        assert set(map(tuple, got.tolist())) == {p for p in brute if sel[p[0]] or sel[p[1]]}
