@@ -66,7 +66,7 @@ extern "C" {
 #define LA_STATUS_BAD_PARAM 0x40u /* la_energy_forces_device: negative or non-finite epsilon, sigma, q */
 
 /* ---- energy terms reported by la_energy_forces ---- */
-#define LA_PAIR_VARIANTS 6
+#define LA_PAIR_VARIANTS 3
 #define LA_MAX_WALKERS 256 /* walkers per handle, over all its systems */
 #define LA_N_TERMS 7 /* LJ, RF, soft-core LJ, scaled RF, bond, angle, restraint */
 
@@ -148,10 +148,9 @@ typedef struct {
     int32_t autotune;            /* 1: pick pair-kernel launch shape by timing at create */
     double list_capacity_factor; /* >= 1 safety factor on list capacities (default 1.6) */
     int32_t pair_variant;        /* pair kernel when not autotuned, [0, LA_PAIR_VARIANTS):
-                                    scalar FP32 0 = 8 warps/CTA with 80 registers (default),
-                                    1 = 4 warps/72, 2 = 4 warps/64; packed FP32x2 3 = 4
-                                    warps/80, 4 = 4 warps/96, 5 = 8 warps/80.  All give
-                                    identical results. */
+                                    0 = 8 warps/CTA with 80 registers (default), 1 = 4
+                                    warps/72, 2 = 4 warps/64.  All give identical
+                                    results. */
     int32_t pair_ctas_per_sm;    /* pair grid in 8-warp CTA equivalents per SM (0 = 4) */
     int32_t chunk_entries;       /* cluster-pair entries per warp work item, a multiple of
                                     32 (0 = 32) */

@@ -8,7 +8,7 @@ number of walkers and MD steps) the spread of Delta A over independent seeds
 measures each method's statistical efficiency.
 
     python -m paper_2307_08006_gb300.compare --system harmonic --seeds 5
-    python -m paper_2307_08006_gb300.compare --sweep --steps 20000
+    python -m paper_2307_08006_gb300.compare --sweep --steps 200000 --seeds 3
 """
 from __future__ import annotations
 
@@ -78,40 +78,61 @@ def compare(name: str, n_steps: int, seeds: Sequence[int], windows_per_stage: in
     return res
 
 
-def sweep(n_steps: int, seeds: Sequence[int], masses: Sequence[float], frictions: Sequence[float]) -> List[Dict]:
-    """Delta A spread and lambda mobility of the solvation-like workload for
-    lambda-particle masses (kJ/mol ps^2) and frictions (ps^-1), SI S2."""
-    spec = synth.water_box(4096, 12, seed=8007)
-    base = synth.water_run(seed=8007, walkers_per_stage=8, n_bins=100, n_full=200.0, skin=0.15)
+def sweep_system(name: str):
+    """(spec, run) of the systems the mass / friction sweep runs on: the
+    256-water two-stage system (20 bins per stage) or the 4096-water bench
+    workload (100 bins per stage)."""
+    if name == "water256":
+        spec = synth.water_box(256, 4, seed=8010, box=1.984, r_cut=0.85)
+        return spec, synth.water_run(seed=8010, walkers_per_stage=4, n_bins=20)
+    if name == "solvation":
+        spec = synth.water_box(4096, 12, seed=8007)
+        return spec, synth.water_run(seed=8007, walkers_per_stage=8, n_bins=100, n_full=200.0, skin=0.15)
+    raise ValueError(name)
+
+
+def sweep(n_steps: int, seeds: Sequence[int], masses: Sequence[float], frictions: Sequence[float],
+          system: str = "water256", every: int = 1000) -> List[Dict]:
+    """Delta A (per stage and summed) and lambda mobility for lambda-particle
+    masses (kJ/mol ps^2) and frictions (ps^-1), SI S2.  Every (mass,
+    friction, seed) is its own system of one batched engine, so the whole
+    sweep advances in one launch sequence per step."""
+    spec, base = sweep_system(system)
+    combos = [(float(m), float(g), int(sd)) for m in masses for g in frictions for sd in seeds]
+    inputs = []
+    for m, g, sd in combos:
+        r = replace(base, m_lambda=m, gamma_lambda=g, seed=sd)
+        inputs.append(labf.SystemInput(spec, r, synth.initial_state(spec, r, seed=sd + 7)))
+    eng = labf.Engine(inputs, options=dict(graph_steps=20))
+    W = eng.n_walkers
+    lam_min, lam_max = np.full(W, np.inf), np.full(W, -np.inf)
+    done = 0
+    while done < n_steps:
+        k = min(every, n_steps - done)
+        eng.step(k)
+        done += k
+        lam = eng.get_states()["lam"]
+        lam_min, lam_max = np.minimum(lam_min, lam), np.maximum(lam_max, lam)
+    per = {}
+    w0 = 0
+    for si, (m, g, sd) in enumerate(combos):
+        nw = inputs[si].run.n_walkers
+        abf = [eng.read_abf(si, k) for k in range(len(base.stages))]
+        empty = int(sum(int((a["count"] == 0).sum()) for a in abf))
+        per.setdefault((m, g), []).append(dict(dA=[a["dA"] for a in abf], empty=empty,
+                                               span=float(np.mean(lam_max[w0:w0 + nw] - lam_min[w0:w0 + nw]))))
+        w0 += nw
+    eng.close()
     rows = []
-    for m in masses:
-        for g in frictions:
-            run = replace(base, m_lambda=float(m), gamma_lambda=float(g))
-            dAs, spans, empty = [], [], []
-            for sd in seeds:
-                r = replace(run, seed=int(sd))
-                st = synth.initial_state(spec, r, seed=int(sd) + 7)
-                eng = labf.engine_for(spec, r, st, options=dict(graph_steps=20))
-                lam_min = np.full(r.n_walkers, np.inf)
-                lam_max = np.full(r.n_walkers, -np.inf)
-                done = 0
-                while done < n_steps:
-                    k = min(1000, n_steps - done)
-                    eng.step(k)
-                    done += k
-                    lam = np.array([eng.get_state(w)["lam"] for w in range(r.n_walkers)])
-                    lam_min, lam_max = np.minimum(lam_min, lam), np.maximum(lam_max, lam)
-                abf = [eng.read_abf(0, s) for s in range(len(r.stages))]
-                empty.append(int(sum(int((a["count"] == 0).sum()) for a in abf)))
-                dAs.append(sum(a["dA"] for a in abf))
-                spans.append(float(np.mean(lam_max - lam_min)))
-                eng.close()
-            ok = [v for v, e in zip(dAs, empty) if e == 0]
-            rows.append(dict(m_lambda=m, gamma_lambda=g,
-                             dA_mean=float(np.mean(ok)) if ok else None,
-                             dA_std=float(np.std(ok, ddof=1)) if len(ok) > 1 else None,
-                             empty_bins=empty, lambda_span=float(np.mean(spans)), steps=n_steps,
-                             seeds=len(seeds)))
+    for (m, g), rs in per.items():
+        ok = [r["dA"] for r in rs if r["empty"] == 0]
+        tot = [sum(d) for d in ok]
+        rows.append(dict(m_lambda=m, gamma_lambda=g, system=system, steps=n_steps, seeds=len(rs),
+                         dA_mean=float(np.mean(tot)) if ok else None,
+                         dA_std=float(np.std(tot, ddof=1)) if len(ok) > 1 else None,
+                         dA_stage_mean=[float(np.mean([d[k] for d in ok])) for k in range(len(base.stages))]
+                         if ok else None,
+                         empty_bins=[r["empty"] for r in rs], lambda_span=float(np.mean([r["span"] for r in rs]))))
     return rows
 
 
@@ -122,11 +143,12 @@ def main():
     ap.add_argument("--seeds", type=int, default=5)
     ap.add_argument("--windows", type=int, default=10)
     ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--sweep-system", default="water256", choices=["water256", "solvation"])
     args = ap.parse_args()
     seeds = [8100 + k for k in range(args.seeds)]
     if args.sweep:
         m0 = synth.M_LAMBDA_KJ_PS2
-        for row in sweep(args.steps, seeds, [m0 / 10, m0, m0 * 10], [100.0, 1000.0]):
+        for row in sweep(args.steps, seeds, [m0 / 10, m0, m0 * 10], [100.0, 1000.0], system=args.sweep_system):
             print(json.dumps(row))
     else:
         print(json.dumps(compare(args.system, args.steps, seeds, args.windows)))

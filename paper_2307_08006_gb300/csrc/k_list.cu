@@ -324,8 +324,9 @@ __global__ void k_permute_scatter(Dev d, int g0, int g1) {
 }
 
 // -------------------------------------------------------------------------
-// R8: cluster-pair list.  One warp per (super-cluster S, candidate column
-// slot k): the k-th column (with its periodic image) within reach of S's box.
+// R8: cluster-pair list.  One warp per work item (super-cluster S, run of
+// LB_CHUNK candidate column slots k): the k-th column (with its periodic
+// image) within reach of S's box.
 // For every candidate super-cluster T of that column (cyclic half rule) T's
 // 64 slots are staged in shared memory, the 16 x 8 (j-cluster, i-cluster)
 // box tests run lane-parallel, and for each passing pair of clusters lane
@@ -351,9 +352,11 @@ __device__ __forceinline__ bool excluded_meta(int a, int2 ma, int4 ea, int b, in
 }
 
 constexpr int LB_WARPS = 4;
+constexpr int LB_CHUNK = 4;  // candidate-column slots per work item
 
-// work items (S, k) are handed out by a global counter (counters[8]); the
-// last warp out (counters[9]) resets both for the next launch
+// work items (S, run of LB_CHUNK candidate-column slots) of the walkers that
+// rebuild are handed out by a global counter (counters[8]); the last warp
+// out (counters[9]) resets both for the next launch
 constexpr int CTR_LB_ITEM = 8, CTR_LB_DONE = 9;
 
 __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, int w1) {
@@ -363,167 +366,202 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
     __shared__ int2 s_m[LB_WARPS][SC], t_m[LB_WARPS][SC];
     __shared__ int4 s_e[LB_WARPS][SC], t_e[LB_WARPS][SC];
     __shared__ int4 s_bb[LB_WARPS][2 * NIC + 2], t_bb[LB_WARPS][2 * NJC];
-    const int s_begin = d.walk[w0].sc_off, s_end = d.walk[w1 - 1].sc_off + d.walk[w1 - 1].sc_cap;
-    const long long total = (long long)(s_end - s_begin) * d.ncs;
+    __shared__ int s_pre[LA_MAX_WALKERS_PER_LAUNCH + 1], s_wk[LA_MAX_WALKERS_PER_LAUNCH];
+    __shared__ int s_nw;
+    const int nchunk = (d.ncs + LB_CHUNK - 1) / LB_CHUNK;
+    // prefix of the work items over the walkers that rebuild (their actual
+    // super-clusters only), so that walkers without a rebuild cost nothing
+    if (wib == 0) {
+        int acc = 0, nw = 0;
+        for (int base = w0; base < w1; base += 32) {
+            const int w = base + lane;
+            const bool on = w < w1 && d.rebuild[w] != 0;
+            int units = on ? d.n_sc[w] * nchunk : 0, rank = on ? 1 : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int a = __shfl_up_sync(0xffffffffu, units, o), b = __shfl_up_sync(0xffffffffu, rank, o);
+                if (lane >= o) {
+                    units += a;
+                    rank += b;
+                }
+            }
+            if (on) {
+                s_pre[nw + rank - 1] = acc + units - d.n_sc[w] * nchunk;
+                s_wk[nw + rank - 1] = w;
+            }
+            acc += __shfl_sync(0xffffffffu, units, 31);
+            nw += __shfl_sync(0xffffffffu, rank, 31);
+        }
+        if (lane == 0) {
+            s_pre[nw] = acc;
+            s_nw = nw;
+        }
+    }
+    __syncthreads();
+    const int nw_on = s_nw;
+    const long long total = s_pre[nw_on];
     for (;;) {
         long long idx = 0;
         if (lane == 0) idx = (long long)atomicAdd(&d.counters[CTR_LB_ITEM], 1ull);
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= total) break;
-        const int s = s_begin + (int)(idx / d.ncs), kslot = (int)(idx % d.ncs);
-        int lo = w0, hi = w1 - 1;
+        int lo = 0, hi = nw_on - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (d.walk[mid].sc_off <= s) lo = mid; else hi = mid - 1;
+            if (s_pre[mid] <= idx) lo = mid; else hi = mid - 1;
         }
-        const int w = lo;
-        if (!d.rebuild[w]) continue;
-        const WalkerDev &W = d.walk[w];
-        const SysDev &S = d.sys[W.sys];
-        const int S_loc = s - W.sc_off;
-        const int nsc = d.n_sc[w];
-        const size_t sub = (size_t)s * d.ncs + kslot;
-        if (S_loc >= nsc || kslot >= S.cspan * S.cspan) {
-            if (lane == 0) d.sub_n[sub] = 0;
-            continue;
-        }
-        const int4 slo = d.bb_sc[2 * (size_t)s], shi = d.bb_sc[2 * (size_t)s + 1];
-        const int ncx = S.ncx;
-        const int cx0 = (int)(((long long)(slo.x - S.Rq) * ncx) >> 24);
-        const int cx1 = (int)(((long long)(shi.x + S.Rq) * ncx) >> 24);
-        const int cy0 = (int)(((long long)(slo.y - S.Rq) * ncx) >> 24);
-        const int cy1 = (int)(((long long)(shi.y + S.Rq) * ncx) >> 24);
-        const int cx = cx0 + kslot % S.cspan, cy = cy0 + kslot / S.cspan;
-        if (cx > cx1 || cy > cy1) {
-            if (lane == 0) d.sub_n[sub] = 0;
-            continue;
-        }
-        if (kslot == 0 && lane == 0 && (cx1 - cx0 >= S.cspan || cy1 - cy0 >= S.cspan))
-            set_status(d, LA_STATUS_LIST_OVERFLOW);  // cannot happen for boxes inside a column
-        const int gS = W.slot_off + S_loc * SC;
-        __syncwarp();
-        // staged .w: the atom id, or -1 for a slot without normal pairs
-        // (padding or alchemical)
-        for (int k = lane; k < SC; k += 32) {
-            int4 u = d.uq[gS + k];
-            int2 m = d.smeta[gS + k];
-            const int4 e = d.sexcl[gS + k];
-            if (m.y) u.w = -1;
-            m.y = (e.x & e.y & e.z & e.w) != -1;  // staged .y: the slot has extra exclusions
-            s_u[wib][k] = u;
-            s_m[wib][k] = m;
-            s_e[wib][k] = e;
-        }
-        if (lane < 2 * NIC) s_bb[wib][lane] = d.bb_ic[2 * (size_t)s * NIC + lane];
-        __syncwarp();
-        const long long R = S.R;
-        const int U = 1 << 24;
-        const int ty = floordiv(cy, ncx), wy = cy - ty * ncx;
-        const int tx = floordiv(cx, ncx), wx = cx - tx * ncx;
-        const int col = wx + ncx * wy;
-        const int t0 = d.col_sc[W.col_off + col], tn = d.col_nsc[W.col_off + col];
-        int nent = 0;
-        const size_t ebase = sub * d.sub_cap;
-        for (int T_loc = t0; T_loc < t0 + tn && T_loc < nsc; ++T_loc) {
-            // cyclic half list over super-clusters: T is S's partner when it
-            // lies less than half-way round the index circle
-            if (T_loc != S_loc) {
-                const int del = T_loc > S_loc ? T_loc - S_loc : T_loc - S_loc + nsc;
-                if (2 * del > nsc || (2 * del == nsc && T_loc < S_loc)) continue;
+        const int w = s_wk[lo];
+        const int local = (int)(idx - s_pre[lo]);
+        const int s = d.walk[w].sc_off + local / nchunk;
+        const int k0 = (local % nchunk) * LB_CHUNK;
+        for (int kslot = k0; kslot < k0 + LB_CHUNK && kslot < d.ncs; ++kslot) {
+            const WalkerDev &W = d.walk[w];
+            const SysDev &S = d.sys[W.sys];
+            const int S_loc = s - W.sc_off;
+            const int nsc = d.n_sc[w];
+            const size_t sub = (size_t)s * d.ncs + kslot;
+            if (kslot >= S.cspan * S.cspan) {
+                if (lane == 0) d.sub_n[sub] = 0;
+                continue;
             }
-            const int t = W.sc_off + T_loc;
-            const int4 tlo = d.bb_sc[2 * (size_t)t], thi = d.bb_sc[2 * (size_t)t + 1];
-            if (tlo.w == 0) continue;
-            unsigned zpass = 0;  // z shifts whose super-cluster boxes are in range
-            for (int tz = -1; tz <= 1; ++tz) {
-                if (T_loc == S_loc && (tx < 0 || (tx == 0 && (ty < 0 || (ty == 0 && tz < 0))))) continue;
-                if (bb_dist2(slo, shi, tlo, thi, tx * U, ty * U, tz * U) < R) zpass |= 1u << (tz + 1);
+            const int4 slo = d.bb_sc[2 * (size_t)s], shi = d.bb_sc[2 * (size_t)s + 1];
+            const int ncx = S.ncx;
+            const int cx0 = (int)(((long long)(slo.x - S.Rq) * ncx) >> 24);
+            const int cx1 = (int)(((long long)(shi.x + S.Rq) * ncx) >> 24);
+            const int cy0 = (int)(((long long)(slo.y - S.Rq) * ncx) >> 24);
+            const int cy1 = (int)(((long long)(shi.y + S.Rq) * ncx) >> 24);
+            const int cx = cx0 + kslot % S.cspan, cy = cy0 + kslot / S.cspan;
+            if (cx > cx1 || cy > cy1) {
+                if (lane == 0) d.sub_n[sub] = 0;
+                continue;
             }
-            if (!zpass) continue;
-            const int gT = W.slot_off + T_loc * SC;
+            if (kslot == 0 && lane == 0 && (cx1 - cx0 >= S.cspan || cy1 - cy0 >= S.cspan))
+                set_status(d, LA_STATUS_LIST_OVERFLOW);  // cannot happen for boxes inside a column
+            const int gS = W.slot_off + S_loc * SC;
             __syncwarp();
+            // staged .w: the atom id, or -1 for a slot without normal pairs
+            // (padding or alchemical)
             for (int k = lane; k < SC; k += 32) {
-                int4 u = d.uq[gT + k];
-                int2 m = d.smeta[gT + k];
-                const int4 e = d.sexcl[gT + k];
+                int4 u = d.uq[gS + k];
+                int2 m = d.smeta[gS + k];
+                const int4 e = d.sexcl[gS + k];
                 if (m.y) u.w = -1;
-                m.y = (e.x & e.y & e.z & e.w) != -1;
-                t_u[wib][k] = u;
-                t_m[wib][k] = m;
-                t_e[wib][k] = e;
+                m.y = (e.x & e.y & e.z & e.w) != -1;  // staged .y: the slot has extra exclusions
+                s_u[wib][k] = u;
+                s_m[wib][k] = m;
+                s_e[wib][k] = e;
             }
-            t_bb[wib][lane] = d.bb_jc[2 * (size_t)t * NJC + lane];
+            if (lane < 2 * NIC) s_bb[wib][lane] = d.bb_ic[2 * (size_t)s * NIC + lane];
             __syncwarp();
-            for (int tz = -1; tz <= 1; ++tz) {
-                if (!(zpass & (1u << (tz + 1)))) continue;
-                const int shx = tx * U, shy = ty * U, shz = tz * U;
-                const bool self0 = (T_loc == S_loc) && tx == 0 && ty == 0 && tz == 0;
-                const int shift_bits = (tx + 1) | ((ty + 1) << 2) | ((tz + 1) << 4);
-                // lane-parallel box tests of the 128 (jc, ic) combinations:
-                // bit (jc & 3) * 8 + ic of word jc >> 2
-                unsigned cm0, cm1, cm2, cm3;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int c = lane + 32 * q, jc = c >> 3, ic = c & 7;
-                    const int4 jlo = t_bb[wib][2 * jc], jhi = t_bb[wib][2 * jc + 1];
-                    const int4 ilo = s_bb[wib][2 * ic], ihi = s_bb[wib][2 * ic + 1];
-                    const bool ok = jlo.w > 0 && ilo.w > 0 && bb_dist2(ilo, ihi, jlo, jhi, shx, shy, shz) < R;
-                    const unsigned b = __ballot_sync(0xffffffffu, ok);
-                    if (q == 0) cm0 = b; else if (q == 1) cm1 = b; else if (q == 2) cm2 = b; else cm3 = b;
+            const long long R = S.R;
+            const int U = 1 << 24;
+            const int ty = floordiv(cy, ncx), wy = cy - ty * ncx;
+            const int tx = floordiv(cx, ncx), wx = cx - tx * ncx;
+            const int col = wx + ncx * wy;
+            const int t0 = d.col_sc[W.col_off + col], tn = d.col_nsc[W.col_off + col];
+            int nent = 0;
+            const size_t ebase = sub * d.sub_cap;
+            for (int T_loc = t0; T_loc < t0 + tn && T_loc < nsc; ++T_loc) {
+                // cyclic half list over super-clusters: T is S's partner when it
+                // lies less than half-way round the index circle
+                if (T_loc != S_loc) {
+                    const int del = T_loc > S_loc ? T_loc - S_loc : T_loc - S_loc + nsc;
+                    if (2 * del > nsc || (2 * del == nsc && T_loc < S_loc)) continue;
                 }
-                // j-clusters with at least one candidate i-cluster, ascending
-                unsigned jmask = 0;
-#pragma unroll
-                for (int t4 = 0; t4 < 4; ++t4) {
-                    jmask |= ((cm0 >> (8 * t4)) & 0xffu) ? 1u << t4 : 0u;
-                    jmask |= ((cm1 >> (8 * t4)) & 0xffu) ? 1u << (4 + t4) : 0u;
-                    jmask |= ((cm2 >> (8 * t4)) & 0xffu) ? 1u << (8 + t4) : 0u;
-                    jmask |= ((cm3 >> (8 * t4)) & 0xffu) ? 1u << (12 + t4) : 0u;
+                const int t = W.sc_off + T_loc;
+                const int4 tlo = d.bb_sc[2 * (size_t)t], thi = d.bb_sc[2 * (size_t)t + 1];
+                if (tlo.w == 0) continue;
+                unsigned zpass = 0;  // z shifts whose super-cluster boxes are in range
+                for (int tz = -1; tz <= 1; ++tz) {
+                    if (T_loc == S_loc && (tx < 0 || (tx == 0 && (ty < 0 || (ty == 0 && tz < 0))))) continue;
+                    if (bb_dist2(slo, shi, tlo, thi, tx * U, ty * U, tz * U) < R) zpass |= 1u << (tz + 1);
                 }
-                for (; jmask; jmask &= jmask - 1u) {
-                    const int jc = __ffs(jmask) - 1;
-                    const unsigned cw = jc < 8 ? (jc < 4 ? cm0 : cm1) : (jc < 12 ? cm2 : cm3);
-                    const unsigned cand = (cw >> ((jc & 3) * 8)) & 0xffu;
-                    const int4 uj = t_u[wib][jc * JC + jb];
-                    const int2 mj = t_m[wib][jc * JC + jb];
-                    const int4 ej = t_e[wib][jc * JC + jb];
-                    const int ujx = uj.x + shx, ujy = uj.y + shy, ujz = uj.z + shz;
-                    const int jlim = self0 ? jc * JC + jb : SC;  // same cluster set: slot_i < slot_j
-                    unsigned lbyte = 0;
-                    for (unsigned m = cand; m; m &= m - 1u) {  // candidate i-clusters, ascending
-                        const int ic = __ffs(m) - 1;
-                        const int si = ic * IC + ia;
-                        const int4 ui = s_u[wib][si];
-                        const int2 mi = s_m[wib][si];
-                        // D < R implies every component lies in (-2^23, 2^23) (R <= 2^46
-                        // because L >= 2 r_list), i.e. this shift is the minimum image
-                        const int dx = ujx - ui.x, dy = ujy - ui.y, dz = ujz - ui.z;
-                        bool ok = (ui.w | uj.w) >= 0 && si < jlim &&
-                                  (long long)dx * dx + (long long)dy * dy + (long long)dz * dz < R &&
-                                  !(mi.x >= 0 && mi.x == mj.x);
-                        if (ok && (mi.y | mj.y))  // extra partner lists
-                            ok = !excluded_meta(ui.w, mi, s_e[wib][si], uj.w, mj, ej);
-                        lbyte |= (unsigned)ok << ic;
+                if (!zpass) continue;
+                const int gT = W.slot_off + T_loc * SC;
+                __syncwarp();
+                for (int k = lane; k < SC; k += 32) {
+                    int4 u = d.uq[gT + k];
+                    int2 m = d.smeta[gT + k];
+                    const int4 e = d.sexcl[gT + k];
+                    if (m.y) u.w = -1;
+                    m.y = (e.x & e.y & e.z & e.w) != -1;
+                    t_u[wib][k] = u;
+                    t_m[wib][k] = m;
+                    t_e[wib][k] = e;
+                }
+                t_bb[wib][lane] = d.bb_jc[2 * (size_t)t * NJC + lane];
+                __syncwarp();
+                for (int tz = -1; tz <= 1; ++tz) {
+                    if (!(zpass & (1u << (tz + 1)))) continue;
+                    const int shx = tx * U, shy = ty * U, shz = tz * U;
+                    const bool self0 = (T_loc == S_loc) && tx == 0 && ty == 0 && tz == 0;
+                    const int shift_bits = (tx + 1) | ((ty + 1) << 2) | ((tz + 1) << 4);
+                    // lane-parallel box tests of the 128 (jc, ic) combinations:
+                    // bit (jc & 3) * 8 + ic of word jc >> 2
+                    unsigned cm0, cm1, cm2, cm3;
+    #pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int c = lane + 32 * q, jc = c >> 3, ic = c & 7;
+                        const int4 jlo = t_bb[wib][2 * jc], jhi = t_bb[wib][2 * jc + 1];
+                        const int4 ilo = s_bb[wib][2 * ic], ihi = s_bb[wib][2 * ic + 1];
+                        const bool ok = jlo.w > 0 && ilo.w > 0 && bb_dist2(ilo, ihi, jlo, jhi, shx, shy, shz) < R;
+                        const unsigned b = __ballot_sync(0xffffffffu, ok);
+                        if (q == 0) cm0 = b; else if (q == 1) cm1 = b; else if (q == 2) cm2 = b; else cm3 = b;
                     }
-                    const unsigned imask = __reduce_or_sync(0xffffffffu, lbyte);
-                    if (imask) {
-                        if (nent < d.sub_cap) {
-                            const size_t e = ebase + nent;
-                            // i-cluster mask twice: bits 8-15 are pruned by the batched
-                            // step, bits 16-23 keep the listed set
-                            if (lane == 0)
-                                d.sub_hdr[e] = make_int2(gT + jc * JC, shift_bits | (int)(imask << 8) | (int)(imask << 16));
-                            d.sub_lb[32 * e + lane] = (unsigned char)lbyte;
-                        } else if (lane == 0) {
-                            set_status(d, LA_STATUS_LIST_OVERFLOW);
+                    // j-clusters with at least one candidate i-cluster, ascending
+                    unsigned jmask = 0;
+    #pragma unroll
+                    for (int t4 = 0; t4 < 4; ++t4) {
+                        jmask |= ((cm0 >> (8 * t4)) & 0xffu) ? 1u << t4 : 0u;
+                        jmask |= ((cm1 >> (8 * t4)) & 0xffu) ? 1u << (4 + t4) : 0u;
+                        jmask |= ((cm2 >> (8 * t4)) & 0xffu) ? 1u << (8 + t4) : 0u;
+                        jmask |= ((cm3 >> (8 * t4)) & 0xffu) ? 1u << (12 + t4) : 0u;
+                    }
+                    for (; jmask; jmask &= jmask - 1u) {
+                        const int jc = __ffs(jmask) - 1;
+                        const unsigned cw = jc < 8 ? (jc < 4 ? cm0 : cm1) : (jc < 12 ? cm2 : cm3);
+                        const unsigned cand = (cw >> ((jc & 3) * 8)) & 0xffu;
+                        const int4 uj = t_u[wib][jc * JC + jb];
+                        const int2 mj = t_m[wib][jc * JC + jb];
+                        const int4 ej = t_e[wib][jc * JC + jb];
+                        const int ujx = uj.x + shx, ujy = uj.y + shy, ujz = uj.z + shz;
+                        const int jlim = self0 ? jc * JC + jb : SC;  // same cluster set: slot_i < slot_j
+                        unsigned lbyte = 0;
+                        for (unsigned m = cand; m; m &= m - 1u) {  // candidate i-clusters, ascending
+                            const int ic = __ffs(m) - 1;
+                            const int si = ic * IC + ia;
+                            const int4 ui = s_u[wib][si];
+                            const int2 mi = s_m[wib][si];
+                            // D < R implies every component lies in (-2^23, 2^23) (R <= 2^46
+                            // because L >= 2 r_list), i.e. this shift is the minimum image
+                            const int dx = ujx - ui.x, dy = ujy - ui.y, dz = ujz - ui.z;
+                            bool ok = (ui.w | uj.w) >= 0 && si < jlim &&
+                                      (long long)dx * dx + (long long)dy * dy + (long long)dz * dz < R &&
+                                      !(mi.x >= 0 && mi.x == mj.x);
+                            if (ok && (mi.y | mj.y))  // extra partner lists
+                                ok = !excluded_meta(ui.w, mi, s_e[wib][si], uj.w, mj, ej);
+                            lbyte |= (unsigned)ok << ic;
                         }
-                        ++nent;
+                        const unsigned imask = __reduce_or_sync(0xffffffffu, lbyte);
+                        if (imask) {
+                            if (nent < d.sub_cap) {
+                                const size_t e = ebase + nent;
+                                // i-cluster mask twice: bits 8-15 are pruned by the batched
+                                // step, bits 16-23 keep the listed set
+                                if (lane == 0)
+                                    d.sub_hdr[e] = make_int2(gT + jc * JC, shift_bits | (int)(imask << 8) | (int)(imask << 16));
+                                d.sub_lb[32 * e + lane] = (unsigned char)lbyte;
+                            } else if (lane == 0) {
+                                set_status(d, LA_STATUS_LIST_OVERFLOW);
+                            }
+                            ++nent;
+                        }
                     }
                 }
             }
+            if (lane == 0) d.sub_n[sub] = min(nent, d.sub_cap);
+            __syncwarp();
         }
-        if (lane == 0) d.sub_n[sub] = min(nent, d.sub_cap);
-        __syncwarp();
     }
     // the last warp out resets the work counters for the next launch
     if (lane == 0) {
@@ -549,6 +587,10 @@ __global__ void k_listcompact(Dev d, int w0, int w1) {
             if (d.walk[mid].sc_off <= s) lo = mid; else hi = mid - 1;
         }
         if (!d.rebuild[lo]) continue;
+        if (s - d.walk[lo].sc_off >= d.n_sc[lo]) {  // capacity slot without a super-cluster
+            if (lane == 0) d.sc_nent[s] = 0;
+            continue;
+        }
         const size_t ebase = (size_t)s * d.ent_cap;
         int n = 0;
         for (int k = 0; k < d.ncs; ++k) {

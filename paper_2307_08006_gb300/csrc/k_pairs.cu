@@ -13,16 +13,11 @@
 // accumulators stay in registers for the whole item.  Forces are summed in
 // FP32 and added to the 64-bit fixed-point force array with integer atomics
 // (order-free, so results are bit-reproducible).  The i-forces are flushed
-// to the fixed-point array after every 32 entries of a super-cluster's list
-// and each entry's j-force sums the even and the odd i-clusters separately,
+// to the fixed-point array after every 32 entries of a super-cluster's list,
 // so every kernel variant and work-item size (a multiple of 32 entries)
-// produces the same bits.
-//
-// Packed variant: sm_100-family FP32x2 instructions (add/mul/fma .f32x2)
-// evaluate the pairs of two i-clusters (2p, 2p+1) with one instruction per
-// operation; the super-cluster is stored as i-cluster pairs and the j-atoms
-// duplicated into both halves, so operands load as packed registers.  Every
-// packed operation rounds per half exactly as its scalar counterpart.
+// produces the same bits.  All float-to-fixed conversions use integer
+// instructions: the hardware conversion to 64-bit integers runs on the FP64
+// pipe, which is narrow on this GPU.
 //
 // Per in-cutoff pair (force only), 37 FP32 flops (FMA = 2) plus one rsqrt:
 //   d = x_i - x_j (3), r2 (5), 1/r2 (1), sigma_ij = s_i + s_j, (sigma/r)^2,
@@ -177,14 +172,17 @@ __device__ __forceinline__ void item_entries(const Dev &d, PairShared<WARPS> &sh
         unsigned emask = __ballot_sync(FULL, im_l != 0u);
         __syncwarp();
         // one entry: every flagged i-cluster against the entry's j-cluster;
-        // fjs receives j-atom jb's partial force over this lane's i-atoms
+        // fjs receives j-atom jb's partial force over this lane's i-atoms.
+        // The re-pruning form evaluates every listed tile: the atom whose
+        // displacement triggered it may already have moved past the margin
+        // the previous pruning allowed for.
         auto entry = [&](int k, float (&fjs)[3]) {
             const unsigned imask = __shfl_sync(FULL, im_l, k);
             const float4 xj = sh.jx[wib][k][jb];
             const float2 lj_j = sh.jl[wib][k][jb];
             const unsigned lb = sh.lb[wib][k][lane];
             touched |= imask;
-            float fj[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};  // even, odd i-clusters
+            float fj[3] = {0.f, 0.f, 0.f};
             unsigned kb = 0;  // this lane's pairs within r_c + margin, per i-cluster
 #pragma unroll
             for (int ic = 0; ic < NIC; ++ic) {
@@ -208,9 +206,9 @@ __device__ __forceinline__ void item_entries(const Dev &d, PairShared<WARPS> &sh
                     fi[ic][0] = fmaf(fs, dx, fi[ic][0]);
                     fi[ic][1] = fmaf(fs, dy, fi[ic][1]);
                     fi[ic][2] = fmaf(fs, dz, fi[ic][2]);
-                    fj[ic & 1][0] = fmaf(fs, dx, fj[ic & 1][0]);
-                    fj[ic & 1][1] = fmaf(fs, dy, fj[ic & 1][1]);
-                    fj[ic & 1][2] = fmaf(fs, dz, fj[ic & 1][2]);
+                    fj[0] = fmaf(fs, dx, fj[0]);
+                    fj[1] = fmaf(fs, dy, fj[1]);
+                    fj[2] = fmaf(fs, dz, fj[2]);
                     if (ENERGY) {
                         if (in) {
                             elj += e4s6 * (sr6 - 1.f);
@@ -224,9 +222,9 @@ __device__ __forceinline__ void item_entries(const Dev &d, PairShared<WARPS> &sh
                 const unsigned keep = __reduce_or_sync(FULL, kb);
                 keep_l = lane == k ? keep : keep_l;
             }
-            fjs[0] = fj[0][0] + fj[1][0];
-            fjs[1] = fj[0][1] + fj[1][1];
-            fjs[2] = fj[0][2] + fj[1][2];
+            fjs[0] = fj[0];
+            fjs[1] = fj[1];
+            fjs[2] = fj[2];
         };
         // two entries per iteration: the compiler interleaves their
         // independent loads and arithmetic (the order of every sum stays), and
@@ -310,254 +308,6 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
         }
     }
     // the last warp out resets the work counters for the next launch
-    if (lane == 0) {
-        __threadfence();
-        const unsigned long long done = atomicAdd(&d.counters[CTR_DONE], 1ull);
-        if (done == (unsigned long long)nblk * WARPS - 1ull) {
-            d.counters[CTR_ITEM] = 0ull;
-            d.counters[CTR_DONE] = 0ull;
-            __threadfence();
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// packed FP32x2 normal pairs (forces only)
-// ---------------------------------------------------------------------------
-typedef unsigned long long f32x2;  // two FP32 values in one 64-bit register pair
-
-__device__ __forceinline__ f32x2 pk(float a, float b) {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float2 upk(f32x2 v) {
-    float2 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-    return r;
-}
-__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
-    f32x2 r;
-    asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
-    f32x2 r;
-    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-    f32x2 r;
-    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 r;
-    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
-constexpr int EPC2 = 16;  // entries prepared per pass in the packed variant (two per i-flush)
-
-template <int WARPS>
-struct PairShared2 {
-    // i-cluster pairs (2p, 2p+1) of the item's super-cluster:
-    // (x_a, x_b, y_a, y_b), (z_a, z_b, q_a, q_b), (s_a, s_b, e_a, e_b)
-    float4 si[WARPS][NIC / 2][IC][3];
-    // prepared j-atoms, each value in both halves: (x, x, y, y), (z, z, q, q), (s, s, e, e)
-    float4 sj[WARPS][EPC2][JC][3];
-    unsigned char lb[WARPS][EPC2][32];
-    int pre[LA_MAX_WALKERS_PER_LAUNCH + 1];
-};
-
-// one work item of the packed form (PRUNE as in item_entries).  Per entry the
-// lane's j-atom is read once (three packed registers pairs of duplicated
-// values); per flagged i-cluster pair one unit evaluates the lane's pairs with
-// i-clusters 2p and 2p+1 together, each packed operation rounding per half as
-// its scalar counterpart, so the sums equal the scalar variants' bit for bit.
-template <int WARPS, int MSHIFT, bool PRUNE>
-__device__ __forceinline__ void item_entries_x2(const Dev &d, PairShared2<WARPS> &sh, const SysDev &S, int4 it,
-                                                int gS) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int ia = lane & 7, jb = lane >> 3;
-    const float L = S.boxf, rc2 = S.rc2, rp2 = S.rprune2;
-    const f32x2 nkrf2 = pk(-2.0f * S.krf, -2.0f * S.krf);
-    f32x2 fi[NIC / 2][3];
-#pragma unroll
-    for (int p = 0; p < NIC / 2; ++p) fi[p][0] = fi[p][1] = fi[p][2] = 0ull;
-    unsigned touched = 0;
-    const size_t ebase = (size_t)it.x * d.ent_cap;
-    for (int eb = it.y; eb < it.z; eb += EPC2) {
-        const int ne = min(EPC2, it.z - eb);
-        int gj_l = 0, hy_l = 0;
-        unsigned im_l = 0, keep_l = 0;
-        __syncwarp();
-        if (lane < ne) {
-            const int2 hdr = d.ent_hdr[ebase + eb + lane];
-            gj_l = hdr.x;
-            hy_l = hdr.y;
-            im_l = ((unsigned)hdr.y >> (PRUNE ? 16 : MSHIFT)) & 0xffu;
-            const float sx = (float)((hdr.y & 3) - 1) * L;
-            const float sy = (float)(((hdr.y >> 2) & 3) - 1) * L;
-            const float sz = (float)(((hdr.y >> 4) & 3) - 1) * L;
-#pragma unroll
-            for (int q = 0; q < JC; ++q) {
-                float4 x = d.xq[gj_l + q];
-                const float2 l = d.lj[gj_l + q];
-                x.x += sx;
-                x.y += sy;
-                x.z += sz;
-                sh.sj[wib][lane][q][0] = make_float4(x.x, x.x, x.y, x.y);
-                sh.sj[wib][lane][q][1] = make_float4(x.z, x.z, x.w, x.w);
-                sh.sj[wib][lane][q][2] = make_float4(l.x, l.x, l.y, l.y);
-            }
-            const uint4 *src = reinterpret_cast<const uint4 *>(d.ent_lb + 32 * (ebase + eb + lane));
-            uint4 *dst = reinterpret_cast<uint4 *>(&sh.lb[wib][lane][0]);
-            dst[0] = src[0];
-            dst[1] = src[1];
-        }
-        unsigned emask = __ballot_sync(FULL, im_l != 0u);  // entries with tiles left
-        __syncwarp();
-        auto entry = [&](int k, float (&fjs)[3]) {
-            const unsigned imask = __shfl_sync(FULL, im_l, k);
-            const unsigned lb = sh.lb[wib][k][lane];
-            const float4 J0 = sh.sj[wib][k][jb][0], J1 = sh.sj[wib][k][jb][1], J2 = sh.sj[wib][k][jb][2];
-            const f32x2 xj = pk(J0.x, J0.y), yj = pk(J0.z, J0.w), zj = pk(J1.x, J1.y);
-            const f32x2 qj = pk(J1.z, J1.w), sgj = pk(J2.x, J2.y), ej = pk(J2.z, J2.w);
-            touched |= imask;
-            f32x2 fjx = 0ull, fjy = 0ull, fjz = 0ull;  // (even, odd) i-clusters
-            unsigned kb = 0;  // this lane's pairs within r_c + margin, per i-cluster
-#pragma unroll
-            for (int p = 0; p < NIC / 2; ++p) {
-                if (imask & (3u << (2 * p))) {
-                    const float4 I0 = sh.si[wib][p][ia][0], I1 = sh.si[wib][p][ia][1];
-                    const float4 I2 = sh.si[wib][p][ia][2];
-                    const f32x2 dx = sub2(pk(I0.x, I0.y), xj);
-                    const f32x2 dy = sub2(pk(I0.z, I0.w), yj);
-                    const f32x2 dz = sub2(pk(I1.x, I1.y), zj);
-                    const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
-                    const float2 r2s = upk(r2);
-                    const bool la = (lb >> (2 * p)) & 1u, lbb = (lb >> (2 * p + 1)) & 1u;
-                    if (PRUNE) {
-                        kb |= (la && r2s.x < rp2) ? 1u << (2 * p) : 0u;
-                        kb |= (lbb && r2s.y < rp2) ? 2u << (2 * p) : 0u;
-                    }
-                    const bool ina = la && (r2s.x < rc2);
-                    const bool inb = lbb && (r2s.y < rc2);
-                    const f32x2 rinv = pk(rsqrtf(r2s.x), rsqrtf(r2s.y));
-                    const f32x2 r2inv = mul2(rinv, rinv);
-                    const f32x2 sg = add2(pk(I2.x, I2.y), sgj);
-                    const f32x2 sr2 = mul2(mul2(sg, sg), r2inv);
-                    const f32x2 sr6 = mul2(mul2(sr2, sr2), sr2);
-                    const f32x2 e4s6 = mul2(mul2(pk(I2.z, I2.w), ej), sr6);
-                    const f32x2 qq = mul2(pk(I1.z, I1.w), qj);
-                    const float2 s6 = upk(sr6);  // 12 s^6 - 6 with immediate operands
-                    const f32x2 t = pk(fmaf(12.f, s6.x, -6.f), fmaf(12.f, s6.y, -6.f));
-                    const f32x2 b = fma2(qq, rinv, mul2(e4s6, t));
-                    float2 f = upk(fma2(b, r2inv, mul2(qq, nkrf2)));
-                    f.x = ina ? f.x : 0.f;
-                    f.y = inb ? f.y : 0.f;
-                    const f32x2 fs = pk(f.x, f.y);
-                    fi[p][0] = fma2(fs, dx, fi[p][0]);
-                    fi[p][1] = fma2(fs, dy, fi[p][1]);
-                    fi[p][2] = fma2(fs, dz, fi[p][2]);
-                    fjx = fma2(fs, dx, fjx);
-                    fjy = fma2(fs, dy, fjy);
-                    fjz = fma2(fs, dz, fjz);
-                }
-            }
-            if (PRUNE) {
-                const unsigned keep = __reduce_or_sync(FULL, kb);
-                keep_l = lane == k ? keep : keep_l;
-            }
-            const float2 jx = upk(fjx), jy = upk(fjy), jz = upk(fjz);
-            fjs[0] = jx.x + jx.y;
-            fjs[1] = jy.x + jy.y;
-            fjs[2] = jz.x + jz.y;
-        };
-        while (emask) {
-            const int k0 = __ffs(emask) - 1;
-            emask &= emask - 1u;
-            float a[3], b[3] = {0.f, 0.f, 0.f};
-            const int gA = __shfl_sync(FULL, gj_l, k0) + jb;
-            int gB = 0;
-            const bool two = emask != 0u;
-            if (!PRUNE && two) {
-                const int k1 = __ffs(emask) - 1;
-                emask &= emask - 1u;
-                gB = __shfl_sync(FULL, gj_l, k1) + jb;
-                entry(k0, a);
-                entry(k1, b);
-            } else {
-                entry(k0, a);
-            }
-            flush_j2(d, gA, gB, !PRUNE && two, ia, a, b);
-        }
-        // the i-forces at the same 32-entry boundaries as the scalar variants
-        if (((eb - it.y) & 31) == 32 - EPC2 || eb + EPC2 >= it.z) {
-            float fs[NIC][3];
-#pragma unroll
-            for (int p = 0; p < NIC / 2; ++p) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float2 t = upk(fi[p][c]);
-                    fs[2 * p][c] = t.x;
-                    fs[2 * p + 1][c] = t.y;
-                    fi[p][c] = 0ull;
-                }
-            }
-            flush_i(d, gS, ia, jb, touched, fs);
-            touched = 0;
-        }
-        if (PRUNE && lane < ne) d.ent_hdr[ebase + eb + lane].y = (hy_l & ~0xff00) | (int)(keep_l << 8);
-    }
-}
-
-template <int WARPS>
-__device__ __noinline__ void item_entries_x2_prune(const Dev &d, PairShared2<WARPS> &sh, const SysDev &S, int4 it,
-                                                   int gS) {
-    item_entries_x2<WARPS, 8, true>(d, sh, S, it, gS);
-}
-
-template <int WARPS, int MSHIFT>
-__device__ __forceinline__ void normal_items_x2(const Dev &d, int w0, int w1, int nblk, PairShared2<WARPS> &sh) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nw = w1 - w0;
-    const int total = sh.pre[nw];
-    for (;;) {
-        int v = 0;
-        if (lane == 0) v = (int)atomicAdd(&d.counters[CTR_ITEM], 1ull);
-        v = __shfl_sync(FULL, v, 0);
-        if (v >= total) break;
-        int lo = 0, hi = nw - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (sh.pre[mid] <= v) lo = mid; else hi = mid - 1;
-        }
-        const int w = w0 + lo;
-        const WalkerDev &W = d.walk[w];
-        const SysDev &S = d.sys[W.sys];
-        const int4 it = d.items[W.item_base + (v - sh.pre[lo])];
-        const int sc = it.x;
-        const int gS = W.slot_off + (sc - W.sc_off) * SC;
-        __syncwarp();
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {  // slots lane and lane + 32
-            const int sl = lane + 32 * h2;
-            const int ic = sl >> 3, p = ic >> 1, h = ic & 1;
-            const float4 x = d.xq[gS + sl];
-            const float2 l = d.lj[gS + sl];
-            float *f = reinterpret_cast<float *>(&sh.si[wib][p][sl & 7][0]);
-            f[h] = x.x;
-            f[2 + h] = x.y;
-            f[4 + h] = x.z;
-            f[6 + h] = x.w;
-            f[8 + h] = l.x;
-            f[10 + h] = l.y;
-        }
-        if (MSHIFT == 8 && d.prune_now[w] != 0ull) item_entries_x2_prune<WARPS>(d, sh, S, it, gS);
-        else item_entries_x2<WARPS, MSHIFT, false>(d, sh, S, it, gS);
-    }
     if (lane == 0) {
         __threadfence();
         const unsigned long long done = atomicAdd(&d.counters[CTR_DONE], 1ull);
@@ -731,9 +481,8 @@ __device__ __forceinline__ void bonded_items(const Dev &d, int w0, int w1, int b
 }
 
 // WARPS x 32 threads per CTA; MINB: resident CTAs per SM the register
-// allocation is sized for.  Variants (autotuned): scalar 8 warps / 3 CTAs (80
-// registers), 4 warps / 7 CTAs (72), 4 warps / 8 CTAs (64); packed 4 warps /
-// 6 CTAs (80), 4 warps / 5 CTAs (96), 8 warps / 3 CTAs (80).
+// allocation is sized for.  Variants (autotuned): 8 warps / 3 CTAs (80
+// registers), 4 warps / 7 CTAs (72), 4 warps / 8 CTAs (64).
 template <bool ENERGY, int WARPS, int MINB, bool FUSED>
 __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(Dev d, int w0, int w1, int nblk_pairs, int a0, int a1,
                                                           int nblk_bonded) {
@@ -761,32 +510,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs(Dev d, int w0, int w
     normal_items<ENERGY, WARPS, FUSED ? 8 : 16>(d, w0, w1, nblk_pairs, sh);
 }
 
-template <int WARPS, int MINB, bool FUSED>
-__global__ void __launch_bounds__(WARPS * 32, MINB) k_pairs_x2(Dev d, int w0, int w1, int nblk_pairs, int a0, int a1,
-                                                          int nblk_bonded) {
-    __shared__ PairShared2<WARPS> sh;
-    const int nblk_alch = gridDim.x - nblk_pairs - nblk_bonded;
-    if ((int)blockIdx.x < nblk_alch) {
-        alch_items<false, WARPS, FUSED>(d, w0, w1, a0, a1, blockIdx.x, nblk_alch);
-        return;
-    }
-    if (FUSED && (int)blockIdx.x < nblk_alch + nblk_bonded) {
-        bonded_items(d, w0, w1, blockIdx.x - nblk_alch, nblk_bonded);
-        return;
-    }
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int w = w0; w < w1; ++w) {
-            sh.pre[w - w0] = acc;
-            acc += d.n_items[w];
-        }
-        sh.pre[w1 - w0] = acc;
-    }
-    __syncthreads();
-    normal_items_x2<WARPS, FUSED ? 8 : 16>(d, w0, w1, nblk_pairs, sh);
-}
-
-template <bool ENERGY, int WARPS, int MINB, bool X2 = false>
+template <bool ENERGY, int WARPS, int MINB>
 static void launch_pairs_v(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t s, bool fused = false) {
     int nblk = hv.pair_blocks * 8 / WARPS;  // pair_blocks counts 8-warp CTAs
     if (w1 - w0 < hv.n_walkers) {           // a subset of walkers: size the grid to its work
@@ -805,13 +529,8 @@ static void launch_pairs_v(const Dev &d, const HostView &hv, int w0, int w1, cud
         bblk = bblk > hv.n_sm ? hv.n_sm : bblk;
     }
     const int grid = ablk + bblk + nblk;
-    if (fused) {
-        if constexpr (X2) k_pairs_x2<WARPS, MINB, true><<<grid, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1, bblk);
-        else k_pairs<ENERGY, WARPS, MINB, true><<<grid, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1, bblk);
-    } else {
-        if constexpr (X2) k_pairs_x2<WARPS, MINB, false><<<grid, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1, 0);
-        else k_pairs<ENERGY, WARPS, MINB, false><<<grid, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1, 0);
-    }
+    if (fused) k_pairs<ENERGY, WARPS, MINB, true><<<grid, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1, bblk);
+    else k_pairs<ENERGY, WARPS, MINB, false><<<grid, WARPS * 32, 0, s>>>(d, w0, w1, nblk, a0, a1, 0);
 }
 
 void launch_pairs_fused(const Dev &d, const HostView &hv, int n_stages, cudaStream_t s) {
@@ -819,9 +538,6 @@ void launch_pairs_fused(const Dev &d, const HostView &hv, int n_stages, cudaStre
     (void)n_stages;
     if (hv.pair_variant == 1) launch_pairs_v<false, 4, 7>(d, hv, 0, W, s, true);
     else if (hv.pair_variant == 2) launch_pairs_v<false, 4, 8>(d, hv, 0, W, s, true);
-    else if (hv.pair_variant == 3) launch_pairs_v<false, 4, 6, true>(d, hv, 0, W, s, true);
-    else if (hv.pair_variant == 4) launch_pairs_v<false, 4, 5, true>(d, hv, 0, W, s, true);
-    else if (hv.pair_variant == 5) launch_pairs_v<false, 8, 3, true>(d, hv, 0, W, s, true);
     else launch_pairs_v<false, 8, 3>(d, hv, 0, W, s, true);
 }
 
@@ -829,9 +545,6 @@ void launch_pairs(const Dev &d, const HostView &hv, int w0, int w1, bool energy,
     if (energy) launch_pairs_v<true, 8, 3>(d, hv, w0, w1, s);
     else if (hv.pair_variant == 1) launch_pairs_v<false, 4, 7>(d, hv, w0, w1, s);
     else if (hv.pair_variant == 2) launch_pairs_v<false, 4, 8>(d, hv, w0, w1, s);
-    else if (hv.pair_variant == 3) launch_pairs_v<false, 4, 6, true>(d, hv, w0, w1, s);
-    else if (hv.pair_variant == 4) launch_pairs_v<false, 4, 5, true>(d, hv, w0, w1, s);
-    else if (hv.pair_variant == 5) launch_pairs_v<false, 8, 3, true>(d, hv, w0, w1, s);
     else launch_pairs_v<false, 8, 3>(d, hv, w0, w1, s);
 }
 

@@ -2,6 +2,7 @@
 // the device arena, upload of systems, the batched step as a CUDA graph, the
 // one-walker-per-launch form, read-outs and the launch-shape autotuner.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <array>
@@ -20,6 +21,12 @@
 using namespace labf;
 
 namespace {
+
+// an NVTX range over one C-ABI call (a no-op unless a profiler is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 constexpr size_t ALIGN = 256;
 constexpr int IO_FLOATS_MIN = 1 << 16;
@@ -556,10 +563,8 @@ int refresh_forces(la_handle *h, cudaStream_t s) {
 }
 
 void make_report(la_handle *h) {
-    static const char *vname[LA_PAIR_VARIANTS] = {
-        "scalar, 8 warps/CTA, 80 registers", "scalar, 4 warps/CTA, 72 registers",
-        "scalar, 4 warps/CTA, 64 registers", "packed FP32x2, 4 warps/CTA, 80 registers",
-        "packed FP32x2, 4 warps/CTA, 96 registers", "packed FP32x2, 8 warps/CTA, 80 registers"};
+    static const char *vname[LA_PAIR_VARIANTS] = {"8 warps/CTA, 80 registers", "4 warps/CTA, 72 registers",
+                                                  "4 warps/CTA, 64 registers"};
     char rep[512];
     snprintf(rep, sizeof rep,
              "%s: pair_variant=%d (%s), pair_ctas_per_sm=%d (8-warp CTA equivalents), "
@@ -675,6 +680,7 @@ int la_query_sizes(const la_system_desc *sys, int n_sys, const la_options *opt, 
 
 int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt, void *arena,
                      size_t arena_bytes, void *stream, la_handle **out) {
+    NvtxRange nvtx_range("la_create_system");
     if (!out) return LA_ERR_INVALID_ARG;
     *out = nullptr;
     la_handle *h = new la_handle();
@@ -688,7 +694,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
     if (opt) h->opt = *opt;
     if (h->opt.pair_variant < 0 || h->opt.pair_variant >= LA_PAIR_VARIANTS ||
         (h->opt.chunk_entries > 0 && h->opt.chunk_entries % 32 != 0)) {
-        h->err = "pair_variant must be in [0, 6) and chunk_entries a multiple of 32";
+        h->err = "pair_variant must be in [0, LA_PAIR_VARIANTS) and chunk_entries a multiple of 32";
         *out = h;
         return LA_ERR_INVALID_ARG;
     }
@@ -1021,6 +1027,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
 }
 
 int la_step_walkers(la_handle *h, int64_t n_steps, void *stream) {
+    NvtxRange nvtx_range("la_step_walkers");
     if (!h) return LA_ERR_INVALID_ARG;
     if (n_steps < 0) return fail(h, LA_ERR_INVALID_ARG, "n_steps < 0");
     int rc = check_posted(h);
@@ -1042,6 +1049,7 @@ int la_step_walkers(la_handle *h, int64_t n_steps, void *stream) {
 }
 
 int la_step_walkers_plain(la_handle *h, int64_t n_steps, void *stream) {
+    NvtxRange nvtx_range("la_step_walkers_plain");
     if (!h) return LA_ERR_INVALID_ARG;
     if (n_steps < 0) return fail(h, LA_ERR_INVALID_ARG, "n_steps < 0");
     int rc = check_posted(h);
@@ -1076,6 +1084,7 @@ int la_step_walkers_plain(la_handle *h, int64_t n_steps, void *stream) {
 
 int la_read_abf(la_handle *h, int sys, int stage, double *sum, double *sumsq, int64_t *count, double *grad,
                 double *A, double *dA, double *dA_se, void *stream) {
+    NvtxRange nvtx_range("la_read_abf");
     if (!h) return LA_ERR_INVALID_ARG;
     if (sys < 0 || sys >= (int)h->sys.size() || stage < 0 || stage >= h->sys_nstage[sys])
         return fail(h, LA_ERR_INVALID_ARG, "bad system/stage");
@@ -1118,6 +1127,7 @@ int la_read_abf(la_handle *h, int sys, int stage, double *sum, double *sumsq, in
 
 int la_energy_forces(la_handle *h, int walker, uint32_t flags, double *energy_terms, float *forces, double *dUdl,
                      double *dUdtheta, double *d2Udl_dtheta, void *stream) {
+    NvtxRange nvtx_range("la_energy_forces");
     if (!h) return LA_ERR_INVALID_ARG;
     if (walker < 0 || walker >= h->L.W) return fail(h, LA_ERR_INVALID_ARG, "bad walker");
     if (h->sticky != LA_OK) return fail(h, LA_ERR_STATE, "handle in error state: %s", h->err.c_str());
@@ -1151,6 +1161,7 @@ int la_energy_forces(la_handle *h, int walker, uint32_t flags, double *energy_te
 
 int la_energy_forces_device(la_handle *h, int walker, const float *x, const double *theta, const double *lam,
                             double *out, float *forces, void *stream) {
+    NvtxRange nvtx_range("la_energy_forces_device");
     if (!h) return LA_ERR_INVALID_ARG;
     if (walker < 0 || walker >= h->L.W) return fail(h, LA_ERR_INVALID_ARG, "bad walker");
     int rc = check_posted(h);
@@ -1232,6 +1243,7 @@ int la_set_state(la_handle *h, int walker, const float *x, const float *v, const
 }
 
 int la_get_states(la_handle *h, float *x, float *v, double *lam, double *plam, uint64_t *step, void *stream) {
+    NvtxRange nvtx_range("la_get_states");
     if (!h) return LA_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int W = h->L.W;
@@ -1257,6 +1269,7 @@ int la_get_states(la_handle *h, float *x, float *v, double *lam, double *plam, u
 
 int la_set_states(la_handle *h, const float *x, const float *v, const double *lam, const double *plam,
                   const uint64_t *step, void *stream) {
+    NvtxRange nvtx_range("la_set_states");
     if (!h) return LA_ERR_INVALID_ARG;
     if (h->sticky != LA_OK) return fail(h, LA_ERR_STATE, "handle in error state: %s", h->err.c_str());
     cudaStream_t s = (cudaStream_t)stream;
@@ -1322,6 +1335,7 @@ uint64_t fingerprint(const la_handle *h) {
 }  // namespace
 
 int la_checkpoint_save(la_handle *h, void *buf, size_t cap, size_t *bytes, void *stream) {
+    NvtxRange nvtx_range("la_checkpoint_save");
     if (!h || !bytes) return LA_ERR_INVALID_ARG;
     const size_t need = sizeof(CkptHeader) + h->state_bytes;
     *bytes = need;
@@ -1345,6 +1359,7 @@ int la_checkpoint_save(la_handle *h, void *buf, size_t cap, size_t *bytes, void 
 }
 
 int la_checkpoint_load(la_handle *h, const void *buf, size_t bytes, void *stream) {
+    NvtxRange nvtx_range("la_checkpoint_load");
     if (!h || !buf) return LA_ERR_INVALID_ARG;
     CkptHeader hd;
     if (bytes < sizeof hd) return fail(h, LA_ERR_INVALID_ARG, "checkpoint too short");
@@ -1367,6 +1382,7 @@ int la_checkpoint_load(la_handle *h, const void *buf, size_t bytes, void *stream
 }
 
 int la_set_alch_params(la_handle *h, int sys, const double *theta, void *stream) {
+    NvtxRange nvtx_range("la_set_alch_params");
     if (!h || !theta) return LA_ERR_INVALID_ARG;
     if (sys < 0 || sys >= (int)h->sys.size()) return fail(h, LA_ERR_INVALID_ARG, "bad system");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1394,6 +1410,7 @@ int la_set_alch_params(la_handle *h, int sys, const double *theta, void *stream)
 }
 
 int la_abf_export(la_handle *h, int sys, int stage, double *sum, double *sumsq, int64_t *count, void *stream) {
+    NvtxRange nvtx_range("la_abf_export");
     if (!h || !sum || !sumsq || !count) return LA_ERR_INVALID_ARG;
     if (sys < 0 || sys >= (int)h->sys.size() || stage < 0 || stage >= h->sys_nstage[sys])
         return fail(h, LA_ERR_INVALID_ARG, "bad system/stage");
@@ -1425,6 +1442,7 @@ int la_abf_export(la_handle *h, int sys, int stage, double *sum, double *sumsq, 
 
 int la_abf_import(la_handle *h, int sys, int stage, const double *sum, const double *sumsq, const int64_t *count,
                   void *stream) {
+    NvtxRange nvtx_range("la_abf_import");
     if (!h || !sum || !sumsq || !count) return LA_ERR_INVALID_ARG;
     if (sys < 0 || sys >= (int)h->sys.size() || stage < 0 || stage >= h->sys_nstage[sys])
         return fail(h, LA_ERR_INVALID_ARG, "bad system/stage");
@@ -1461,6 +1479,7 @@ int la_abf_import(la_handle *h, int sys, int stage, const double *sum, const dou
 
 int la_read_theta(la_handle *h, int sys, int stage, double *sum_d2, double *sum_d, double *sum_sd,
                   double *dA_dtheta, void *stream) {
+    NvtxRange nvtx_range("la_read_theta");
     if (!h) return LA_ERR_INVALID_ARG;
     if (sys < 0 || sys >= (int)h->sys.size() || stage < 0 || stage >= h->sys_nstage[sys])
         return fail(h, LA_ERR_INVALID_ARG, "bad system/stage");
@@ -1518,6 +1537,7 @@ int la_read_theta(la_handle *h, int sys, int stage, double *sum_d2, double *sum_
 
 int la_get_pairs(la_handle *h, int walker, int32_t *pairs, uint8_t *kind, int64_t cap, int64_t *count,
                  void *stream) {
+    NvtxRange nvtx_range("la_get_pairs");
     if (!h || !count) return LA_ERR_INVALID_ARG;
     if (walker < 0 || walker >= h->L.W) return fail(h, LA_ERR_INVALID_ARG, "bad walker");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1638,6 +1658,7 @@ int la_stats(la_handle *h, int64_t *out, void *stream) {
 }
 
 int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_out, void *stream) {
+    NvtxRange nvtx_range("la_time_kernels");
     if (!h || !ms_out || n_steps <= 0) return LA_ERR_INVALID_ARG;
     int rc = check_posted(h);
     if (rc != LA_OK) return rc;
@@ -1696,6 +1717,7 @@ int la_time_kernels(la_handle *h, int n_steps, float *ms_out, int64_t *launches_
 }
 
 int la_autotune(la_handle *h, void *stream) {
+    NvtxRange nvtx_range("la_autotune");
     if (!h) return LA_ERR_INVALID_ARG;
     int rc = check_posted(h);
     if (rc != LA_OK) return rc;

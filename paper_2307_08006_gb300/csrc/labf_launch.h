@@ -12,8 +12,7 @@ namespace labf {
 // Host copies of the per-walker offsets the launchers size grids with.
 struct HostView {
     int n_walkers = 0, n_sm = 0, pair_blocks = 0, ncs = 1;
-    int pair_variant = 0;  // scalar 0: 8 warps/CTA, 80 regs; 1: 4 warps, 72; 2: 4 warps, 64;
-                           // packed FP32x2 3: 4 warps, 80; 4: 4 warps, 96; 5: 8 warps, 80
+    int pair_variant = 0;  // 0: 8 warps/CTA, 80 regs; 1: 4 warps, 72; 2: 4 warps, 64
     const int *slot_off = nullptr, *slot_cap = nullptr, *sc_cap = nullptr, *n_cols = nullptr;
     const int *alch_base = nullptr, *n_alch = nullptr, *item_cap = nullptr;
     const int *bo_off = nullptr, *n_bo = nullptr;

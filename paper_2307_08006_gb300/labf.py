@@ -20,7 +20,7 @@ from . import build as _build
 LA_OK = 0
 LA_WARN_EMPTY_BIN = 1
 LA_N_TERMS = 7
-LA_PAIR_VARIANTS = 6
+LA_PAIR_VARIANTS = 3
 LA_MAX_WALKERS = 256
 LA_N_STATS = 7
 LA_N_KERNELS = 6

@@ -264,8 +264,7 @@ def test_pair_kernel_launch_shapes_bit_identical():
     run = synth.water_run(walkers_per_stage=2, n_bins=20)
     st = synth.initial_state(sp, run, lam0=[0.1, 0.3, 0.6, 0.8])
     outs = []
-    shapes = [(0, 4, 32), (1, 7, 32), (2, 8, 64), (1, 2, 64), (0, 1, 32),
-              (3, 4, 32), (4, 6, 64), (5, 3, 32), (3, 1, 96)]
+    shapes = [(0, 4, 32), (1, 7, 32), (2, 8, 64), (1, 2, 64), (0, 1, 32), (2, 3, 96), (1, 6, 64)]
     assert {v for v, _, _ in shapes} == set(range(labf.LA_PAIR_VARIANTS))
     for var, ctas, chunk in shapes:
         e, _ = make_engine(sp, run, state=st, pair_variant=var, pair_ctas_per_sm=ctas, chunk_entries=chunk)
@@ -281,7 +280,7 @@ def test_pair_kernel_launch_shapes_bit_identical():
         make_engine(sp, run, state=st, chunk_entries=48)
 
 
-@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("variant", range(labf.LA_PAIR_VARIANTS))
 def test_dynamic_pruning_skips_tiles_without_changing_results(variant):
     """The batched step's pair pass re-prunes a walker's tiles (keeping those
     with a listed pair within r_c + margin) whenever one of its atoms moved

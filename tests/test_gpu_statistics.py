@@ -133,3 +133,20 @@ def test_theta_gradient_both_estimators_closed_form_gpu_and_oracle():
     assert ep_gpu == pytest.approx(exact, abs=0.01)
     assert ep_cpu == pytest.approx(exact, abs=0.015)
     assert abs(ti_gpu - ep_gpu) < 0.025
+
+
+def test_mass_friction_sweep_driver_runs():
+    """The lambda mass / friction sweep (SI S2) on the 256-water two-stage
+    system, short: every (mass, friction, seed) system advances, lambda moves,
+    and Delta A is finite wherever every bin has samples."""
+    from paper_2307_08006_gb300 import compare
+
+    m0 = synth.M_LAMBDA_KJ_PS2
+    rows = compare.sweep(3000, [1, 2], [m0 / 10, m0], [100.0], every=1000)
+    assert len(rows) == 2
+    for r in rows:
+        assert r["seeds"] == 2 and np.isfinite(r["lambda_span"]) and r["lambda_span"] > 0.0
+        if r["dA_mean"] is not None:
+            assert np.isfinite(r["dA_mean"])
+    # the lighter lambda particle moves further in the same time
+    assert rows[0]["lambda_span"] > rows[1]["lambda_span"]
