@@ -237,6 +237,9 @@ def bench_uneven(args, stream, peak_tflops):
         rng = np.random.default_rng(8008 + k)
         sp.x = ((sp.x + rng.normal(0.0, 0.01, sp.x.shape)) % sp.box).astype(np.float32)
         run = synth.uneven_run(seed=8008 + k, walkers_per_system=8)
+        # the bench's list skin where the box allows it (2 (r_c + skin) <= L)
+        if sp.box >= 2.0 * (sp.r_cut + args.skin):
+            run.skin = args.skin
         inputs.append(labf.SystemInput(sp, run, synth.initial_state(sp, run)))
     t0 = time.perf_counter()
     eng = labf.Engine(inputs, options=dict(graph_steps=args.graph_steps, autotune=1, prune_margin=args.prune_margin))
@@ -250,7 +253,9 @@ def bench_uneven(args, stream, peak_tflops):
     dt = inputs[0].run.dt
     md = args.md_steps
     _timed_steps(eng, md, stream)  # warm-up
+    rb0 = int(eng.stats()[1])
     ms = sum(_timed_steps(eng, md, stream) for _ in range(3)) / 3.0
+    rebuild_rate = (int(eng.stats()[1]) - rb0) / float(W * 3 * md)
     plain_md = max(5, md // 20)
     _timed_steps(eng, 2, stream, plain=True)
     pms = _timed_steps(eng, plain_md, stream, plain=True)
@@ -258,8 +263,9 @@ def bench_uneven(args, stream, peak_tflops):
     st = eng.stats()
     out = dict(
         workload="batched uneven systems: 8 water boxes (256, 512, 1024, 2048, 3072, 4096, 6144, 8192 waters; "
-                 "4-40-site alchemical solutes; r_c 1.0 nm, 0.85 nm for the 1.98 nm box; list skin 0.1 nm, "
-                 f"pruning margin {args.prune_margin:g} nm), 8 walkers each (64), one CUDA graph, autotuned",
+                 "4-40-site alchemical solutes; r_c 1.0 nm, 0.85 nm for the 1.98 nm box; list skin "
+                 f"{args.skin:g} nm, 0.1 nm for the 1.98 nm box; pruning margin {args.prune_margin:g} nm), "
+                 "8 walkers each (64), one CUDA graph, autotuned",
         walkers=W, atoms_all_walkers=atoms, md_steps=3 * md,
         value=walker_ns_per_day(W, md, dt, ms * 1e-3), unit=UNIT, ms_per_md_step=ms / md,
         pair_interactions_per_s=(pn + pa) * md / (ms * 1e-3), in_cutoff_pairs_per_md_step=pn + pa,
@@ -267,7 +273,7 @@ def bench_uneven(args, stream, peak_tflops):
                         ms_per_md_step=pms / plain_md, note="one walker per launch sequence, no CUDA graph"),
         batched_over_plain=(pms / plain_md) / (ms / md),
         lists=dict(tiles_8x4=int(st[6]), cluster_pair_entries=int(st[5]),
-                   tile_efficiency=pn / max(1, 32 * int(st[6]))),
+                   tile_efficiency=pn / max(1, 32 * int(st[6])), rebuilds_per_walker_md_step=rebuild_rate),
         kernel_ms=dict((k, v[0]) for k, v in kt.items()),
         launch=eng.autotune_report(), setup_s=setup_s)
     pair_ms = kt["pairs"][0]
@@ -286,6 +292,7 @@ def bench_large(args, stream, peak_tflops):
 
     sp = synth.large_complex()
     run = synth.large_complex_run()
+    run.skin = args.skin
     t0 = time.perf_counter()
     eng = labf.Engine([labf.SystemInput(sp, run, synth.initial_state(sp, run))],
                       options=dict(graph_steps=args.graph_steps, autotune=1, prune_margin=args.prune_margin))
@@ -297,7 +304,9 @@ def bench_large(args, stream, peak_tflops):
     W = eng.n_walkers
     md = max(20, args.md_steps // 2)
     _timed_steps(eng, md, stream)
+    rb0 = int(eng.stats()[1])
     ms = sum(_timed_steps(eng, md, stream) for _ in range(3)) / 3.0
+    rebuild_rate = (int(eng.stats()[1]) - rb0) / float(W * 3 * md)
     kt = eng.time_kernels(max(5, args.profile_steps // 2), stream)
     st = eng.stats()
     pair_ms = kt["pairs"][0]
@@ -305,12 +314,13 @@ def bench_large(args, stream, peak_tflops):
     out = dict(
         workload="large synthetic complex: 31000 flexible waters + 3000-site chain (0.15 nm bonds, positional "
                  "restraints) + 40-site alchemical ligand (flat-bottom restraint to the chain), 96040 atoms, "
-                 f"9.92 nm box, r_c 1.2 nm, list skin 0.1 nm, pruning margin {args.prune_margin:g} nm",
+                 f"9.92 nm box, r_c 1.2 nm, list skin {args.skin:g} nm, pruning margin {args.prune_margin:g} nm",
         walkers=W, atoms_per_walker=sp.n, md_steps=3 * md,
         value=walker_ns_per_day(W, md, run.dt, ms * 1e-3), unit=UNIT, ms_per_md_step=ms / md,
         pair_interactions_per_s=(pn + pa) * md / (ms * 1e-3), in_cutoff_pairs_per_md_step=pn + pa,
         lists=dict(tiles_8x4=int(st[6]), cluster_pair_entries=int(st[5]),
-                   tile_efficiency=pn / max(1, 32 * int(st[6]))),
+                   tile_efficiency=pn / max(1, 32 * int(st[6])),
+                   rebuilds_per_walker_md_step=rebuild_rate),
         kernel_ms=dict((k, v[0]) for k, v in kt.items()),
         roofline=dict(bound="alu", achieved=ach, peak=peak_tflops, unit="TFLOP/s", frac=ach / peak_tflops,
                       pair_kernel_ms=pair_ms,

@@ -402,10 +402,12 @@ int la_sync(la_handle *h, void *stream, uint32_t *status_bits);
  *   [5] cluster-pair entries in the current lists (all walkers),
  *   [6] 8 x 4 atom-pair tiles the batched step evaluates (all walkers, after
  *       the last dynamic pruning); each tile is one warp-wide evaluation of
- *       32 candidate pairs.
+ *       32 candidate pairs,
+ *   [7] re-pruning passes of the batched step (summed over walkers) after a
+ *       displacement trigger.
  * Synchronising.
  */
-#define LA_N_STATS 7
+#define LA_N_STATS 8
 int la_stats(la_handle *h, int64_t *out, void *stream);
 
 /*

@@ -788,7 +788,10 @@ __global__ void k_gate(Dev d, int w0, int w1, cudaGraphConditionalHandle handle,
     for (int w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
         const int p = d.prune[w];
         d.prune_now[w] = p ? d.step[w] + 1ull : 0ull;
-        if (p) d.prune[w] = 0;
+        if (p) {
+            d.prune[w] = 0;
+            atomicAdd(&d.counters[10], 1ull);
+        }
         if (d.rebuild[w]) any = 1;
     }
     __syncthreads();

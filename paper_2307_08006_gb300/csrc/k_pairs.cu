@@ -226,9 +226,10 @@ __device__ __forceinline__ void item_entries(const Dev &d, PairShared<WARPS> &sh
             fjs[1] = fj[1];
             fjs[2] = fj[2];
         };
-        // two entries per iteration: the compiler interleaves their
-        // independent loads and arithmetic (the order of every sum stays), and
-        // one transposed reduction serves both j-clusters
+        // two entries per iteration (also in the re-pruning form): the
+        // compiler interleaves their independent loads and arithmetic (the
+        // order of every sum stays), and one transposed reduction serves both
+        // j-clusters
         while (emask) {
             const int k0 = __ffs(emask) - 1;
             emask &= emask - 1u;
@@ -236,7 +237,7 @@ __device__ __forceinline__ void item_entries(const Dev &d, PairShared<WARPS> &sh
             const int gA = __shfl_sync(FULL, gj_l, k0) + jb;
             int gB = 0;
             const bool two = emask != 0u;
-            if (!PRUNE && two) {
+            if (two) {
                 const int k1 = __ffs(emask) - 1;
                 emask &= emask - 1u;
                 gB = __shfl_sync(FULL, gj_l, k1) + jb;
@@ -245,7 +246,7 @@ __device__ __forceinline__ void item_entries(const Dev &d, PairShared<WARPS> &sh
             } else {
                 entry(k0, a);
             }
-            flush_j2(d, gA, gB, !PRUNE && two, ia, a, b);
+            flush_j2(d, gA, gB, two, ia, a, b);
         }
         flush_i(d, gS, ia, jb, touched, fi);  // every 32 entries (EPC)
         touched = 0;
@@ -268,11 +269,14 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nw = w1 - w0;
     const int total = sh.pre[nw];
+    // the next item's index is fetched one item ahead, so that the atomic's
+    // round trip overlaps the current item's work
+    int v_next = 0;
+    if (lane == 0) v_next = (int)atomicAdd(&d.counters[CTR_ITEM], 1ull);
     for (;;) {
-        int v = 0;
-        if (lane == 0) v = (int)atomicAdd(&d.counters[CTR_ITEM], 1ull);
-        v = __shfl_sync(FULL, v, 0);
+        const int v = __shfl_sync(FULL, v_next, 0);
         if (v >= total) break;
+        if (lane == 0) v_next = (int)atomicAdd(&d.counters[CTR_ITEM], 1ull);
         int lo = 0, hi = nw - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;

@@ -1626,7 +1626,7 @@ int la_sync(la_handle *h, void *stream, uint32_t *status_bits) {
 int la_stats(la_handle *h, int64_t *out, void *stream) {
     if (!h) return LA_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned long long c[8];
+    unsigned long long c[12];
     CU(h, cudaMemcpyAsync(c, h->d.counters, sizeof c, cudaMemcpyDeviceToHost, s));
     std::vector<int> nent(h->L.scs), nsc(h->L.W);
     CU(h, cudaMemcpyAsync(nent.data(), h->d.sc_nent, sizeof(int) * nent.size(), cudaMemcpyDeviceToHost, s));
@@ -1653,6 +1653,7 @@ int la_stats(la_handle *h, int64_t *out, void *stream) {
         out[4] = (int64_t)c[2];
         out[5] = ents;
         out[6] = tiles;
+        out[7] = (int64_t)c[10];
     }
     return LA_OK;
 }

@@ -170,6 +170,7 @@ struct Dev {
                                     // step whose pair pass re-prunes the walker's tiles
     unsigned long long *counters; // [0] rebuilds [1] pairs normal [2] pairs alch [4, 5] pair
                                   // work items [6] rebuild events [8, 9] list-build work items
+                                  // [10] re-pruning passes after a displacement trigger
 };
 
 // ---------------------------------------------------------------------------

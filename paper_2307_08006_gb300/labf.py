@@ -22,7 +22,7 @@ LA_WARN_EMPTY_BIN = 1
 LA_N_TERMS = 7
 LA_PAIR_VARIANTS = 3
 LA_MAX_WALKERS = 256
-LA_N_STATS = 7
+LA_N_STATS = 8
 LA_N_KERNELS = 6
 LA_EF_REBUILD = 0x1
 LA_EF_COUNT_PAIRS = 0x2
