@@ -178,22 +178,22 @@ struct Dev {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_status(const Dev &d, unsigned bits) { atomicOr(d.status, bits); }
 
-// round(f * 2^32) as a two's-complement int64, computed from the IEEE-754
-// bits with 32/64-bit integer ALU operations only (a float -> int64
-// conversion instruction would run on the FP64 pipe, which is narrow on this
-// GPU).  f = 1.m * 2^(e-127), so f * 2^32 = M * 2^(e-118) with M = 1.m * 2^23.
-// Halves round away from zero; |f| must stay below 2^30 (the fixed-point
-// range); zeros and denormals give 0.
+// round(f * 2^32) as a two's-complement int64, rounded to nearest (ties to
+// even) and symmetric in sign, from FP32 arithmetic and 32-bit conversions
+// only (a float -> int64 conversion instruction would run on the FP64 pipe,
+// which is narrow on this GPU).  With a = |f|, h = floor(a) and r = a - h,
+// r is exact (the fraction of a float is a float) and so is r 2^32 < 2^32;
+// a 2^32 = h 2^32 + r 2^32 with h 2^32 an even integer, so rounding r 2^32
+// once rounds a 2^32.  |f| is clamped below 2^31 (NaN maps to the clamp):
+// a contribution that large, and any NaN, shows up as a summed force beyond
+// the fixed-point range, which the integrator reports.
 __device__ __forceinline__ unsigned long long f2fix(float f) {
-    const unsigned b = __float_as_uint(f);
-    const int e = (int)((b >> 23) & 0xffu);
-    const unsigned long long M = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
-    const int sh = e - 118;
-    unsigned long long v;
-    if (sh >= 0) v = M << (sh < 39 ? sh : 39);
-    else if (sh > -25) v = (M + (1ull << (-sh - 1))) >> (-sh);
-    else v = 0ull;
-    return (b >> 31) ? (unsigned long long)(-(long long)v) : v;
+    const float a = fminf(fabsf(f), 2147483520.0f);  // largest float below 2^31
+    const float h = floorf(a);
+    const unsigned hi = __float2uint_rz(h);
+    const unsigned lo = __float2uint_rn((a - h) * 4294967296.0f);
+    const unsigned long long v = ((unsigned long long)hi << 32) | lo;
+    return f < 0.f ? (unsigned long long)(-(long long)v) : v;
 }
 
 // Fixed-point force accumulation (2^32 units per force unit).  Integer adds
