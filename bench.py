@@ -330,6 +330,52 @@ def bench_large(args, stream, peak_tflops):
     return out
 
 
+def bench_autograd(args):
+    """Differentiation on the bench system (C4 shape): U and its gradients
+    with respect to the positions, lambda and the solute's (epsilon, sigma,
+    q) through torch.autograd, one walker, at 21 lambda values from 0 to 1.
+    Every call hands the device tensors to the engine, which rebuilds the
+    walker's lists from the positions and evaluates U with the hand-written
+    derivative pass; nothing goes through host memory."""
+    import torch
+
+    from paper_2307_08006_gb300 import autograd, labf, synth
+
+    spec, _ = workload(args.skin)
+    run = synth.water_run(seed=8010, walkers_per_stage=1, skin=args.skin)
+    run.stages = [synth.Stage(0.0, 1.0, 20, 1)]
+    state = synth.initial_state(spec, run, lam0=[0.5])
+    eng = labf.engine_for(spec, run, state)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x = torch.tensor(state.x[0], device=dev, requires_grad=True)
+    th = torch.tensor(autograd.theta_of(spec), dtype=torch.float64, device=dev, requires_grad=True)
+    lams = [torch.tensor(k / 20.0, dtype=torch.float64, device=dev, requires_grad=True) for k in range(21)]
+
+    def sweep():
+        for lt in lams:
+            U = autograd.energy(eng, 0, x, lt, th)
+            torch.autograd.grad(U, [x, lt, th])
+
+    sweep()  # warm-up
+    reps = 3
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a.record()
+    for _ in range(reps):
+        sweep()
+    b.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    n = reps * len(lams)
+    eng.close()
+    return dict(workload="differentiation on the bench system (12300 atoms, one walker): U and dU/dx, "
+                         "dU/dlambda, dU/d(epsilon, sigma, q) of the 12 solute sites through torch.autograd "
+                         "at 21 lambda values; lists rebuilt from x on every call",
+                calls=n, ms_per_call=a.elapsed_time(b) / n, wall_ms_per_call=wall / n * 1e3,
+                note="forward + backward per call, CUDA events on the current stream")
+
+
 def gpu_arm(args):
     import torch
 
@@ -483,6 +529,7 @@ def gpu_arm(args):
     if rank == 0 and world == 1 and not args.no_extra:
         extra["C3"] = bench_uneven(args, stream, peak_tflops)
         extra["C5"] = bench_large(args, stream, peak_tflops)
+        extra["C4"] = bench_autograd(args)
     # the integrator streams per atom: F (24 B), 1/m and noise scale (8),
     # v (16), x (16), reference x (16), slot indices (8) read; x, v (32) and
     # the cleared F (24) written
@@ -565,11 +612,11 @@ def main():
     ap.add_argument("--md-steps", type=int, default=200)
     ap.add_argument("--graph-steps", type=int, default=20)
     ap.add_argument("--settle", type=int, default=2000)
-    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--profile-steps", type=int, default=200)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch and large-complex workloads")
+    ap.add_argument("--no-extra", action="store_true", help="skip the uneven-batch, large-complex and differentiation workloads")
     ap.add_argument("--no-peaks", action="store_true", help="skip the FP32/FP64 FMA peak measurement")
     ap.add_argument("--launch", default="",
                     help="fixed pair-kernel shape, e.g. pair_variant=1,pair_ctas_per_sm=6,chunk_entries=64")

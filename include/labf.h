@@ -55,6 +55,8 @@ extern "C" {
 #define LA_ERR_NONFINITE (-7)       /* NaN/Inf appeared in positions or lambda */
 #define LA_ERR_FIXED_OVERFLOW (-8)  /* a force exceeded the 64-bit fixed-point range */
 #define LA_ERR_STATE (-9)           /* the handle is in a sticky error state */
+#define LA_ERR_BAD_INDEX (-10)      /* range-checked builds (LA_CHECKS): an index read from a
+                                       device list, cell or slot array was out of range */
 
 /* ---- device status bits (la_sync / la_status) ---- */
 #define LA_STATUS_LIST_OVERFLOW 0x1u
@@ -62,7 +64,8 @@ extern "C" {
 #define LA_STATUS_FIXED_OVERFLOW 0x4u
 #define LA_STATUS_COLUMN_OVERFLOW 0x8u
 #define LA_STATUS_ALCH_OVERFLOW 0x10u
-#define LA_STATUS_BAD_INDEX 0x20u /* la_alch_pairs_static: alch_idx entry not an alchemical atom */
+#define LA_STATUS_BAD_INDEX 0x20u /* la_alch_pairs_static: alch_idx entry not an alchemical atom;
+                                     range-checked builds: an index out of range */
 #define LA_STATUS_BAD_PARAM 0x40u /* la_energy_forces_device: negative or non-finite epsilon, sigma, q */
 
 /* ---- energy terms reported by la_energy_forces ---- */

@@ -16,6 +16,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblabf.so")
+# range-checked debug build (-DLA_CHECKS=1), objects in their own folder
+BUILD_CHECKS = os.path.join(BUILD, "checks")
+LIB_CHECKS = os.path.join(BUILD, "liblabf_checks.so")
 SOURCES = ["labf_api.cu", "k_dyn.cu", "k_list.cu", "k_pairs.cu", "k_io.cu", "k_static.cu", "k_peak.cu"]
 HEADERS = ["labf_internal.cuh", "labf_launch.h", "labf_dyn.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,14 +42,18 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.getmtime(dep) > t for dep in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), checks: bool = False) -> str:
+    """Compile the engine; checks=True builds the range-checked debug
+    library (liblabf_checks.so, -DLA_CHECKS=1) instead."""
+    odir, lib = (BUILD_CHECKS, LIB_CHECKS) if checks else (BUILD, LIB)
+    extra = [*extra, "-DLA_CHECKS=1"] if checks else list(extra)
+    os.makedirs(odir, exist_ok=True)
     nvcc = _nvcc()
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "labf.h")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(odir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
             jobs.append([nvcc, *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
@@ -60,13 +67,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
         run([nvcc, *ARCH, "-shared", "--cudart", "static", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [], checks="--checks" in sys.argv))

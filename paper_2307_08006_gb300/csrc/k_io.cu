@@ -9,7 +9,7 @@ namespace labf {
 __global__ void k_state_io(Dev d, int w, int n, float *x, float *v, int to_slots) {
     const WalkerDev &W = d.walk[w];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int g = d.slot_of_atom[W.atom_base + i];
+        const int g = checked_slot(d, d.slot_of_atom[W.atom_base + i]);
         if (to_slots) {
             float4 xq = d.xq[g];
             xq.x = x[3 * i];
@@ -32,7 +32,7 @@ __global__ void k_state_io(Dev d, int w, int n, float *x, float *v, int to_slots
 __global__ void k_forces_out(Dev d, int w, int n, float *out) {
     const WalkerDev &W = d.walk[w];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int g = d.slot_of_atom[W.atom_base + i];
+        const int g = checked_slot(d, d.slot_of_atom[W.atom_base + i]);
         const unsigned long long *F = d.F + 3 * (size_t)g;
         out[3 * i] = fix_to_float(F[0]);
         out[3 * i + 1] = fix_to_float(F[1]);
@@ -58,7 +58,7 @@ __global__ void k_lambda_path(const double *lam, int n, double bv, double be, do
 __global__ void k_positions_in(Dev d, int w, int n, const float *x) {
     const WalkerDev &W = d.walk[w];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int g = d.slot_of_atom[W.atom_base + i];
+        const int g = checked_slot(d, d.slot_of_atom[W.atom_base + i]);
         float4 xq = d.xq[g];
         xq.x = x[3 * i];
         xq.y = x[3 * i + 1];

@@ -25,17 +25,19 @@ __global__ void k_quantize(Dev d, int g0, int g1) {
     const int nthr = gridDim.x * blockDim.x;
     for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += nthr) {
         const int w = d.slot_walker[g];
-        if (!d.rebuild[w]) continue;
+        if (!la_in(d, w, d.n_walkers) || !d.rebuild[w]) continue;
         const int a = d.atom_of_slot[g];
         if (a < 0) continue;
         const WalkerDev &W = d.walk[w];
         const SysDev &S = d.sys[W.sys];
+        if (!la_in(d, a, S.n_atoms)) continue;
         const float4 x = d.xq[g];
         const uint32_t ux = quantize(x.x, S.box_inv), uy = quantize(x.y, S.box_inv),
                        uz = quantize(x.z, S.box_inv);
         const int cx = (int)(((unsigned long long)ux * (unsigned)S.ncx) >> 24);
         const int cy = (int)(((unsigned long long)uy * (unsigned)S.ncx) >> 24);
         const int c = cx + S.ncx * cy;
+        if (!la_in(d, c, W.n_cols)) continue;
         d.t_uq[g] = make_int4((int)ux, (int)uy, (int)uz, a);
         d.t_col[g] = c;
         // one atomic per (walker, column) group of the warp's active lanes
@@ -81,10 +83,12 @@ __global__ void k_scatter(Dev d, int g0, int g1) {
     const int nthr = gridDim.x * blockDim.x;
     for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += nthr) {
         const int w = d.slot_walker[g];
-        if (!d.rebuild[w] || d.atom_of_slot[g] < 0) continue;
+        if (!la_in(d, w, d.n_walkers) || !d.rebuild[w] || d.atom_of_slot[g] < 0) continue;
         const WalkerDev &W = d.walk[w];
         const int c = d.t_col[g];
+        if (!la_in(d, c, W.n_cols)) continue;
         const int p = d.col_start[W.col_off + c] + d.t_pos[g];
+        if (!la_in(d, p, d.sys[W.sys].n_atoms)) continue;
         d.bucket[W.atom_base + p] = g;
     }
 }
@@ -103,6 +107,11 @@ __global__ void __launch_bounds__(256) k_colsort(Dev d, int w0) {
         __syncthreads();
         for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
             const int g = d.bucket[W.atom_base + start + k];
+            if (!la_in(d, g, d.n_slots)) {  // sorts last, written as padding
+                key[k] = ~0ull;
+                slot[k] = -1;
+                continue;
+            }
             const int4 u = d.t_uq[g];
             key[k] = ((unsigned long long)(unsigned)u.z << 32) | (unsigned)u.w;
             slot[k] = g;
@@ -149,7 +158,8 @@ __global__ void __launch_bounds__(128) k_kdsplit(Dev d, int w0, int w1) {
         if (s_local >= d.n_sc[w]) continue;
         const int n = d.sc_n[s];
         for (int k = lane; k < SC; k += 32) {
-            const int g = k < n ? d.sc_member[(size_t)s * SC + k] : -1;
+            int g = k < n ? d.sc_member[(size_t)s * SC + k] : -1;
+            if (g >= 0 && !la_in(d, g, d.n_slots)) g = -1;
             if (g >= 0) {
                 const int4 u = d.t_uq[g];
                 sx[wib][k] = u.x; sy[wib][k] = u.y; sz[wib][k] = u.z; sa[wib][k] = u.w;
@@ -268,6 +278,7 @@ __global__ void k_permute_gather(Dev d, int g0, int g1) {
         const int s_local = local / SC;
         int old = -1;
         if (s_local < d.n_sc[w]) old = d.t_old[g];
+        if (old >= 0 && !la_in(d, old, d.n_slots)) old = -1;
         if (old >= 0) {
             d.t_xq[g] = d.xq[old];
             d.t_vv[g] = d.vv[old];
@@ -278,7 +289,7 @@ __global__ void k_permute_gather(Dev d, int g0, int g1) {
             float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
             if (s_local < d.n_sc[w]) {
                 const int first = d.sc_member[(size_t)(W.sc_off + s_local) * SC];
-                if (first >= 0) p = d.xq[first];
+                if (first >= 0 && la_in(d, first, d.n_slots)) p = d.xq[first];
             }
             p.w = 0.f;
             d.t_xq[g] = p;
@@ -296,7 +307,8 @@ __global__ void k_permute_scatter(Dev d, int g0, int g1) {
         if (!d.rebuild[w]) continue;
         const WalkerDev &W = d.walk[w];
         const SysDev &S = d.sys[W.sys];
-        const int a = d.uq[g].w;
+        int a = d.uq[g].w;
+        if (a >= 0 && !la_in(d, a, S.n_atoms)) a = -1;
         float4 x = d.t_xq[g];
         // wrap into [0, L) (the list built from this layout assumes it)
         x.x -= S.boxf * floorf(x.x * S.box_invf);
@@ -458,6 +470,10 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
             const int ty = floordiv(cy, ncx), wy = cy - ty * ncx;
             const int tx = floordiv(cx, ncx), wx = cx - tx * ncx;
             const int col = wx + ncx * wy;
+            if (!la_in(d, col, W.n_cols)) {
+                if (lane == 0) d.sub_n[sub] = 0;
+                continue;
+            }
             const int t0 = d.col_sc[W.col_off + col], tn = d.col_nsc[W.col_off + col];
             int nent = 0;
             const size_t ebase = sub * d.sub_cap;
@@ -638,7 +654,9 @@ __global__ void __launch_bounds__(AL_WARPS * 32) k_alchlist(Dev d, int w0, int w
         const SysDev &S = d.sys[W.sys];
         const int r = it - W.alch_base;
         const int a = d.alch_atoms[S.alch_off + r];
+        if (!la_in(d, a, S.n_atoms)) continue;
         const int ga = d.slot_of_atom[W.atom_base + a];
+        if (!la_in(d, ga, d.n_slots)) continue;
         const int4 ua = d.uq[ga];
         const int2 ma = d.smeta[ga];
         const int4 ea = d.sexcl[ga];

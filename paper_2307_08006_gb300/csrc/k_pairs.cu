@@ -151,6 +151,7 @@ __device__ __forceinline__ void item_entries(const Dev &d, PairShared<WARPS> &sh
             gj_l = hdr.x;
             hy_l = hdr.y;
             im_l = ((unsigned)hdr.y >> (PRUNE ? 16 : MSHIFT)) & 0xffu;
+            if (!la_in(d, gj_l, d.n_slots - JC + 1)) gj_l = 0, im_l = 0;  // entry skipped
             const float sx = (float)((hdr.y & 3) - 1) * L;
             const float sy = (float)(((hdr.y >> 2) & 3) - 1) * L;
             const float sz = (float)(((hdr.y >> 4) & 3) - 1) * L;
@@ -286,6 +287,8 @@ __device__ __forceinline__ void normal_items(const Dev &d, int w0, int w1, int n
         const WalkerDev &W = d.walk[w];
         const SysDev &S = d.sys[W.sys];
         const int4 it = d.items[W.item_base + (v - sh.pre[lo])];
+        if (!la_in(d, it.x - W.sc_off, W.sc_cap) || !la_in(d, it.z - 1, d.ent_cap) || !la_in(d, it.y, it.z))
+            continue;  // item skipped
         const int sc = it.x;
         const int gS = W.slot_off + (sc - W.sc_off) * SC;
         __syncwarp();
@@ -371,8 +374,11 @@ __device__ __forceinline__ void alch_items(const Dev &d, int w0, int w1, int a0,
         const WalkerDev &W = d.walk[w];
         const SysDev &S = d.sys[W.sys];
         const int r = it - W.alch_base;
-        const int a = d.alch_atoms[S.alch_off + r];
-        const int ga = d.slot_of_atom[W.atom_base + a];
+        int a = d.alch_atoms[S.alch_off + r];
+        bool item_ok = la_in(d, a, S.n_atoms);
+        if (!item_ok) a = 0;
+        int ga = d.slot_of_atom[W.atom_base + a];
+        if (!la_in(d, ga, d.n_slots)) ga = W.slot_off, item_ok = false;  // no pairs, still arrives
         const float4 xa = d.xq[ga];
         const float2 la = d.lj[ga];
         double lvd, led, dlvd, dled;
@@ -388,10 +394,11 @@ __device__ __forceinline__ void alch_items(const Dev &d, int w0, int w1, int a0,
         double sv = 0.0, se = 0.0, usc_s = 0.0, urf_s = 0.0;
         double th0 = 0.0, th1 = 0.0, th2 = 0.0, th3 = 0.0, th4 = 0.0, th5 = 0.0;
         int npair = 0;
-        const int cnt = d.alch_cnt[it];
+        const int cnt = item_ok ? d.alch_cnt[it] : 0;
         const int *lst = d.alch_slot + (size_t)it * d.alch_cap;
         for (int k = lane; k < cnt; k += 32) {
             const int gb = lst[k];
+            if (!la_in(d, gb, d.n_slots)) continue;
             const float4 xb = d.xq[gb];
             const float2 lb = d.lj[gb];
             const float dx = min_image(xa.x - xb.x, S.boxf, S.box_invf);

@@ -393,6 +393,7 @@ int status_to_code(unsigned bits) {
     if (bits & LA_STATUS_FIXED_OVERFLOW) return LA_ERR_FIXED_OVERFLOW;
     if (bits & LA_STATUS_NONFINITE) return LA_ERR_NONFINITE;
     if (bits & LA_STATUS_BAD_PARAM) return LA_ERR_INVALID_ARG;
+    if (bits & LA_STATUS_BAD_INDEX) return LA_ERR_BAD_INDEX;
     return LA_OK;
 }
 
@@ -403,6 +404,7 @@ const char *status_text(unsigned bits) {
     if (bits & LA_STATUS_FIXED_OVERFLOW) return "a force exceeded the fixed-point range";
     if (bits & LA_STATUS_NONFINITE) return "non-finite positions or lambda";
     if (bits & LA_STATUS_BAD_PARAM) return "negative or non-finite alchemical parameters";
+    if (bits & LA_STATUS_BAD_INDEX) return "an index read from a device list was out of range (range-checked build)";
     return "ok";
 }
 
@@ -726,6 +728,11 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
     d.max_bins = L.max_bins;
     d.P_max = L.P_max;
     d.chunk = L.chunk;
+    d.n_slots = (int)L.slots;
+    d.n_scs = (int)L.scs;
+    d.n_atoms_w = (int)L.atoms_w;
+    d.n_atoms_s = (int)L.atoms_s;
+    d.n_items_all = (int)L.items;
     d.sys = d_sys;
     d.walk = d_walk;
     d.stage = d_stage;

@@ -27,7 +27,7 @@ __device__ __forceinline__ void bonded_term(const Dev &d, int t, int w0, int w1)
     if (k < S.n_bonds) {
         const int2 ij = d.bond_ij[S.bond_off + k];
         const float2 p = d.bond_p[S.bond_off + k];
-        const int gi = soa[ij.x], gj = soa[ij.y];
+        const int gi = checked_slot(d, soa[ij.x]), gj = checked_slot(d, soa[ij.y]);
         const float4 xi = d.xq[gi], xj = d.xq[gj];
         float dx = min_image(xi.x - xj.x, S.boxf, S.box_invf);
         float dy = min_image(xi.y - xj.y, S.boxf, S.box_invf);
@@ -41,7 +41,7 @@ __device__ __forceinline__ void bonded_term(const Dev &d, int t, int w0, int w1)
     } else if ((k -= S.n_bonds) < S.n_angles) {
         const int4 ijk = d.angle_ijk[S.angle_off + k];
         const float2 p = d.angle_p[S.angle_off + k];
-        const int gi = soa[ijk.x], gj = soa[ijk.y], gk = soa[ijk.z];
+        const int gi = checked_slot(d, soa[ijk.x]), gj = checked_slot(d, soa[ijk.y]), gk = checked_slot(d, soa[ijk.z]);
         const float4 xi = d.xq[gi], xj = d.xq[gj], xk = d.xq[gk];
         float ux = min_image(xi.x - xj.x, S.boxf, S.box_invf);
         float uy = min_image(xi.y - xj.y, S.boxf, S.box_invf);
@@ -71,7 +71,7 @@ __device__ __forceinline__ void bonded_term(const Dev &d, int t, int w0, int w1)
         k -= S.n_angles;
         const int ai = d.posres_idx[S.posres_off + k];
         const float4 x0 = d.posres_x0[S.posres_off + k];
-        const int gi = soa[ai];
+        const int gi = checked_slot(d, soa[ai]);
         const float4 xi = d.xq[gi];
         float dx = min_image(xi.x - x0.x, S.boxf, S.box_invf);
         float dy = min_image(xi.y - x0.y, S.boxf, S.box_invf);
@@ -108,11 +108,11 @@ __device__ __forceinline__ void walker_work(const Dev &d, int w, int lane) {
         for (int grp = 0; grp < 2; ++grp) {
             const int off = S.fb_off + (grp ? S.n_fb_a : 0);
             const int ng = grp ? S.n_fb_b : S.n_fb_a;
-            const float4 r0 = d.xq[soa[d.fb_idx[off]]];
+            const float4 r0 = d.xq[checked_slot(d, soa[d.fb_idx[off]])];
             double acc[4] = {0, 0, 0, 0};
             for (int k = lane; k < ng; k += 32) {
                 const int a = d.fb_idx[off + k];
-                const float4 xa = d.xq[soa[a]];
+                const float4 xa = d.xq[checked_slot(d, soa[a])];
                 const double m = 1.0 / (double)d.ap[S.atom_off + a].w;
                 acc[0] += m * min_image(xa.x - r0.x, S.boxf, S.box_invf);
                 acc[1] += m * min_image(xa.y - r0.y, S.boxf, S.box_invf);
@@ -141,7 +141,7 @@ __device__ __forceinline__ void walker_work(const Dev &d, int w, int lane) {
                 for (int k = lane; k < ng; k += 32) {
                     const int a = d.fb_idx[off + k];
                     const double wgt = (1.0 / (double)d.ap[S.atom_off + a].w) / mt;
-                    add_force(d, soa[a], (float)(sgn * fmag * dv[0] * wgt), (float)(sgn * fmag * dv[1] * wgt),
+                    add_force(d, checked_slot(d, soa[a]), (float)(sgn * fmag * dv[0] * wgt), (float)(sgn * fmag * dv[1] * wgt),
                               (float)(sgn * fmag * dv[2] * wgt));
                 }
             }
@@ -158,7 +158,7 @@ __device__ __forceinline__ void walker_work(const Dev &d, int w, int lane) {
         const double ddmin = S.lr_delta * 3.14159265358979323846 * sinpi(2.0 * lam);
         for (int k = lane; k < S.n_lr; k += 32) {
             const int2 ab = d.lr_ij[S.lr_off + k];
-            const int ga = soa[ab.x], gb = soa[ab.y];
+            const int ga = checked_slot(d, soa[ab.x]), gb = checked_slot(d, soa[ab.y]);
             const float4 xa = d.xq[ga], xb = d.xq[gb];
             const float dx = min_image(xa.x - xb.x, S.boxf, S.box_invf);
             const float dy = min_image(xa.y - xb.y, S.boxf, S.box_invf);
@@ -180,7 +180,7 @@ __device__ __forceinline__ void walker_work(const Dev &d, int w, int lane) {
         const double kl = (1.0 - lam) * S.lh_k0 + lam * S.lh_k1;
         for (int k = lane; k < S.n_lh; k += 32) {
             const int a = d.lh_idx[S.lh_off + k];
-            const int g = soa[a];
+            const int g = checked_slot(d, soa[a]);
             const float4 xa = d.xq[g], x0 = d.lh_x0[S.lh_off + k];
             float dx = min_image(xa.x - x0.x, S.boxf, S.box_invf);
             float dy = min_image(xa.y - x0.y, S.boxf, S.box_invf);

@@ -93,6 +93,8 @@ struct Dev {
     int max_bins, P_max;
     int chunk;                    // entries per pair work item
     int total_bo;
+    // array extents, for the range checks of debug builds (LA_CHECKS)
+    int n_slots, n_scs, n_atoms_w, n_atoms_s, n_items_all;
     const SysDev *sys;
     const WalkerDev *walk;
     const StageDev *stage;
@@ -177,6 +179,25 @@ struct Dev {
 // helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_status(const Dev &d, unsigned bits) { atomicOr(d.status, bits); }
+
+// Debug builds (nvcc -DLA_CHECKS=1; build(checks=True) in the package's
+// build script) range-check every list, cell, slot and atom index read from
+// device memory before it is used: a failed check sets LA_STATUS_BAD_INDEX
+// and the caller skips the access (never a trap).  Release builds compile
+// the checks away.
+#ifndef LA_CHECKS
+#define LA_CHECKS 0
+#endif
+__device__ __forceinline__ bool la_in(const Dev &d, long long i, long long n) {
+    if (!LA_CHECKS) return true;
+    if (i >= 0 && i < n) return true;
+    set_status(d, LA_STATUS_BAD_INDEX);
+    return false;
+}
+
+// a slot index read from a device array, checked in debug builds (a bad one
+// becomes slot 0 once the status bit is set)
+__device__ __forceinline__ int checked_slot(const Dev &d, int g) { return la_in(d, g, d.n_slots) ? g : 0; }
 
 // round(f * 2^32) as a two's-complement int64, rounded to nearest (ties to
 // even) and symmetric in sign, from FP32 arithmetic and 32-bit conversions

@@ -29,7 +29,7 @@ LA_EF_COUNT_PAIRS = 0x2
 TERM_NAMES = ("lj", "rf", "sc_lj", "sc_rf", "bond", "angle", "restraint")
 KERNEL_NAMES = ("integrate", "rebuild", "pairs", "bonded", "walker", "lambda")
 ERRORS = {-1: "INVALID_ARG", -2: "BOX_TOO_SMALL", -3: "CUDA", -4: "UNSUPPORTED", -5: "ARENA_TOO_SMALL",
-          -6: "LIST_OVERFLOW", -7: "NONFINITE", -8: "FIXED_OVERFLOW", -9: "STATE"}
+          -6: "LIST_OVERFLOW", -7: "NONFINITE", -8: "FIXED_OVERFLOW", -9: "STATE", -10: "BAD_INDEX"}
 
 EXPORTED = ("la_query_sizes", "la_create_system", "la_step_walkers", "la_step_walkers_plain",
             "la_read_abf", "la_abf_export", "la_abf_import", "la_energy_forces", "la_get_state", "la_set_state", "la_get_states", "la_set_states",
@@ -86,7 +86,10 @@ _lib = None
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The engine library; with LABF_CHECKS=1 in the environment, the
+    range-checked debug build (every index read from a device list is
+    checked; a bad one is reported as LA_ERR_BAD_INDEX)."""
+    return _build.LIB_CHECKS if os.environ.get("LABF_CHECKS") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = False):
@@ -98,7 +101,7 @@ def load(build_if_missing: bool = False):
     if not os.path.exists(path):
         if not build_if_missing:
             raise ImportError(f"liblabf.so not built at {path}: run __graft_entry__.build()")
-        _build.build()
+        _build.build(checks=path == _build.LIB_CHECKS)
     lib = C.CDLL(path)
     P, I, D, S = C.c_void_p, C.c_int, C.c_double, C.c_size_t
     H = C.c_void_p
