@@ -364,7 +364,7 @@ __device__ __forceinline__ bool excluded_meta(int a, int2 ma, int4 ea, int b, in
 }
 
 constexpr int LB_WARPS = 4;
-constexpr int LB_CHUNK = 4;  // candidate-column slots per work item
+constexpr int LB_CHUNK = 1;  // candidate-column slots per work item
 
 // work items (S, run of LB_CHUNK candidate-column slots) of the walkers that
 // rebuild are handed out by a global counter (counters[8]); the last warp
