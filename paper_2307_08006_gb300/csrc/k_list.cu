@@ -53,23 +53,37 @@ __global__ void k_quantize(Dev d, int g0, int g1) {
     }
 }
 
-// R2: per walker, prefix sums of column counts and super-cluster counts
+// R2: per walker (one warp), prefix sums of column counts and super-cluster
+// counts, 32 columns per pass
 __global__ void k_colscan(Dev d, int w0) {
     const int w = w0 + blockIdx.x;
     if (!d.rebuild[w]) return;
     const WalkerDev &W = d.walk[w];
-    if (threadIdx.x == 0) {
-        int acc = 0, sacc = 0;
-        for (int c = 0; c < W.n_cols; ++c) {
-            const int cnt = d.col_count[W.col_off + c];
-            if (cnt > MAX_COL) set_status(d, LA_STATUS_COLUMN_OVERFLOW);
-            const int nsc = (cnt + SC - 1) / SC;
-            d.col_start[W.col_off + c] = acc;
-            d.col_sc[W.col_off + c] = sacc;
-            d.col_nsc[W.col_off + c] = nsc;
-            acc += cnt;
-            sacc += nsc;
+    const int lane = threadIdx.x & 31;
+    int acc = 0, sacc = 0;  // totals of the previous passes
+    for (int c0 = 0; c0 < W.n_cols; c0 += 32) {
+        const int c = c0 + lane;
+        const int cnt = c < W.n_cols ? d.col_count[W.col_off + c] : 0;
+        if (cnt > MAX_COL) set_status(d, LA_STATUS_COLUMN_OVERFLOW);
+        const int nsc = (cnt + SC - 1) / SC;
+        int a = cnt, b = nsc;  // inclusive warp scans
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ua = __shfl_up_sync(0xffffffffu, a, o), ub = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) {
+                a += ua;
+                b += ub;
+            }
         }
+        if (c < W.n_cols) {
+            d.col_start[W.col_off + c] = acc + a - cnt;
+            d.col_sc[W.col_off + c] = sacc + b - nsc;
+            d.col_nsc[W.col_off + c] = nsc;
+        }
+        acc += __shfl_sync(0xffffffffu, a, 31);
+        sacc += __shfl_sync(0xffffffffu, b, 31);
+    }
+    if (lane == 0) {
         if (sacc > W.sc_cap) {
             set_status(d, LA_STATUS_LIST_OVERFLOW);
             sacc = W.sc_cap;
@@ -592,8 +606,9 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
 }
 
 // R8b: concatenate the sub-lists of each super-cluster in column-slot order
-__global__ void k_listcompact(Dev d, int w0, int w1) {
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(128) k_listcompact(Dev d, int w0, int w1) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    __shared__ int s_off[4][32];
     const int nwarp = gridDim.x * (blockDim.x >> 5);
     const int s_begin = d.walk[w0].sc_off, s_end = d.walk[w1 - 1].sc_off + d.walk[w1 - 1].sc_cap;
     for (int s = s_begin + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < s_end; s += nwarp) {
@@ -609,19 +624,37 @@ __global__ void k_listcompact(Dev d, int w0, int w1) {
         }
         const size_t ebase = (size_t)s * d.ent_cap;
         int n = 0;
-        for (int k = 0; k < d.ncs; ++k) {
-            const size_t sub = (size_t)s * d.ncs + k;
-            const int m = d.sub_n[sub];
-            for (int e = lane; e < m; e += 32) {
-                if (n + e >= d.ent_cap) break;
-                const size_t src = sub * d.sub_cap + e, dst = ebase + n + e;
+        // 32 sub-lists at a time: their sizes by one load per lane and a warp
+        // scan, then every entry of the 32 copied by a flat lane loop (the
+        // sub-list of flat index f found by binary search over the offsets)
+        for (int k0 = 0; k0 < d.ncs; k0 += 32) {
+            const int k = k0 + lane;
+            const int m = k < d.ncs ? d.sub_n[(size_t)s * d.ncs + k] : 0;
+            int incl = m;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            s_off[wib][lane] = incl - m;
+            __syncwarp();
+            for (int f = lane; f < tot && n + f < d.ent_cap; f += 32) {
+                int lo = 0, hi = 31;  // the last sub-list starting at or before f
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[wib][mid] <= f) lo = mid; else hi = mid - 1;
+                }
+                const size_t src = ((size_t)s * d.ncs + k0 + lo) * d.sub_cap + (f - s_off[wib][lo]);
+                const size_t dst = ebase + n + f;
                 d.ent_hdr[dst] = d.sub_hdr[src];
                 const uint4 *ps = reinterpret_cast<const uint4 *>(d.sub_lb + 32 * src);
                 uint4 *pd = reinterpret_cast<uint4 *>(d.ent_lb + 32 * dst);
                 pd[0] = ps[0];
                 pd[1] = ps[1];
             }
-            n += m;
+            __syncwarp();
+            n += tot;
         }
         if (n > d.ent_cap && lane == 0) set_status(d, LA_STATUS_LIST_OVERFLOW);
         if (lane == 0) d.sc_nent[s] = min(n, d.ent_cap);
