@@ -378,6 +378,50 @@ __device__ __forceinline__ bool excluded_meta(int a, int2 ma, int4 ea, int b, in
 }
 
 constexpr int LB_WARPS = 4;
+// Staged slots: coordinates, and in .w a code = exclusion group (bits 0-29)
+// | EXTRA_FLAG when the slot has extra excluded partners.  Slots without
+// normal pairs (padding, alchemical) sit at FAR_I on the i side and FAR_J on
+// the j side (|d| >= 2^30 - 2^24 per component, so D >= R for every list
+// radius, and 3 (2^30 + 2^24)^2 < 2^63); "no group" has a different code on
+// each side, so that one compare decides the group test.
+constexpr int FAR_I = 1 << 29, FAR_J = -(1 << 29);
+constexpr int GROUP_MASK = 0x3fffffff, EXTRA_FLAG = 0x40000000;
+constexpr int NO_GROUP_I = 0x3fffffff, NO_GROUP_J = 0x3ffffffe;
+
+__device__ __forceinline__ int slot_code(int2 m, int4 e, bool i_side) {
+    const int g = m.x >= 0 ? m.x : (i_side ? NO_GROUP_I : NO_GROUP_J);
+    return g | ((e.x & e.y & e.z & e.w) != -1 ? EXTRA_FLAG : 0);
+}
+
+// extra excluded partners of two real atoms (atom ids and lists from memory)
+__device__ __forceinline__ bool excluded_extra(const Dev &d, int gi, int gj) {
+    const int a = d.uq[gi].w, b = d.uq[gj].w;
+    const int4 ea = d.sexcl[gi], eb = d.sexcl[gj];
+    if (ea.x == b || ea.y == b || ea.z == b || ea.w == b) return true;
+    return eb.x == a || eb.y == a || eb.z == a || eb.w == a;
+}
+
+// lane (ia, jb)'s mask byte of one candidate j-cluster: bit ic set when the
+// pair (8 ic + ia of S, slot sj of T) is listed.  SELF: S and T are the
+// same super-cluster with shift 0, where only slot_i < slot_j is listed.
+template <bool SELF>
+__device__ __forceinline__ unsigned tile_masks(const int4 *su, unsigned cand, int ia, int sj, int ujx, int ujy,
+                                               int ujz, int cj, long long R, const Dev &d, int gS, int gT) {
+    unsigned lbyte = 0;
+    for (unsigned m = cand; m; m &= m - 1u) {  // candidate i-clusters, ascending
+        const int ic = __ffs(m) - 1;
+        const int si = ic * IC + ia;
+        const int4 ui = su[si];
+        // D < R implies every component lies in (-2^23, 2^23) (R <= 2^46
+        // because L >= 2 r_list), i.e. this shift is the minimum image
+        const int dx = ujx - ui.x, dy = ujy - ui.y, dz = ujz - ui.z;
+        bool ok = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz < R && ((ui.w ^ cj) & GROUP_MASK) != 0;
+        if (SELF) ok = ok && si < sj;
+        if (ok && ((ui.w | cj) & EXTRA_FLAG)) ok = !excluded_extra(d, gS + si, gT + sj);
+        lbyte |= (unsigned)ok << ic;
+    }
+    return lbyte;
+}
 constexpr int LB_CHUNK = 1;  // candidate-column slots per work item
 
 // work items (S, run of LB_CHUNK candidate-column slots) of the walkers that
@@ -389,8 +433,6 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int ia = lane & 7, jb = lane >> 3;
     __shared__ int4 s_u[LB_WARPS][SC], t_u[LB_WARPS][SC];
-    __shared__ int2 s_m[LB_WARPS][SC], t_m[LB_WARPS][SC];
-    __shared__ int4 s_e[LB_WARPS][SC], t_e[LB_WARPS][SC];
     __shared__ int4 s_bb[LB_WARPS][2 * NIC + 2], t_bb[LB_WARPS][2 * NJC];
     __shared__ int s_pre[LA_MAX_WALKERS_PER_LAUNCH + 1], s_wk[LA_MAX_WALKERS_PER_LAUNCH];
     __shared__ int s_nw;
@@ -465,17 +507,15 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
                 set_status(d, LA_STATUS_LIST_OVERFLOW);  // cannot happen for boxes inside a column
             const int gS = W.slot_off + S_loc * SC;
             __syncwarp();
-            // staged .w: the atom id, or -1 for a slot without normal pairs
-            // (padding or alchemical)
+            // staged: coordinates (FAR_I for a slot without normal pairs) and
+            // the slot code (exclusion group, extra-partner flag)
             for (int k = lane; k < SC; k += 32) {
                 int4 u = d.uq[gS + k];
-                int2 m = d.smeta[gS + k];
+                const int2 m = d.smeta[gS + k];
                 const int4 e = d.sexcl[gS + k];
-                if (m.y) u.w = -1;
-                m.y = (e.x & e.y & e.z & e.w) != -1;  // staged .y: the slot has extra exclusions
+                if (m.y || u.w < 0) u.x = u.y = u.z = FAR_I;
+                u.w = slot_code(m, e, true);
                 s_u[wib][k] = u;
-                s_m[wib][k] = m;
-                s_e[wib][k] = e;
             }
             if (lane < 2 * NIC) s_bb[wib][lane] = d.bb_ic[2 * (size_t)s * NIC + lane];
             __syncwarp();
@@ -511,13 +551,11 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
                 __syncwarp();
                 for (int k = lane; k < SC; k += 32) {
                     int4 u = d.uq[gT + k];
-                    int2 m = d.smeta[gT + k];
+                    const int2 m = d.smeta[gT + k];
                     const int4 e = d.sexcl[gT + k];
-                    if (m.y) u.w = -1;
-                    m.y = (e.x & e.y & e.z & e.w) != -1;
+                    if (m.y || u.w < 0) u.x = u.y = u.z = FAR_J;
+                    u.w = slot_code(m, e, false);
                     t_u[wib][k] = u;
-                    t_m[wib][k] = m;
-                    t_e[wib][k] = e;
                 }
                 t_bb[wib][lane] = d.bb_jc[2 * (size_t)t * NJC + lane];
                 __syncwarp();
@@ -552,26 +590,10 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
                         const unsigned cw = jc < 8 ? (jc < 4 ? cm0 : cm1) : (jc < 12 ? cm2 : cm3);
                         const unsigned cand = (cw >> ((jc & 3) * 8)) & 0xffu;
                         const int4 uj = t_u[wib][jc * JC + jb];
-                        const int2 mj = t_m[wib][jc * JC + jb];
-                        const int4 ej = t_e[wib][jc * JC + jb];
                         const int ujx = uj.x + shx, ujy = uj.y + shy, ujz = uj.z + shz;
-                        const int jlim = self0 ? jc * JC + jb : SC;  // same cluster set: slot_i < slot_j
-                        unsigned lbyte = 0;
-                        for (unsigned m = cand; m; m &= m - 1u) {  // candidate i-clusters, ascending
-                            const int ic = __ffs(m) - 1;
-                            const int si = ic * IC + ia;
-                            const int4 ui = s_u[wib][si];
-                            const int2 mi = s_m[wib][si];
-                            // D < R implies every component lies in (-2^23, 2^23) (R <= 2^46
-                            // because L >= 2 r_list), i.e. this shift is the minimum image
-                            const int dx = ujx - ui.x, dy = ujy - ui.y, dz = ujz - ui.z;
-                            bool ok = (ui.w | uj.w) >= 0 && si < jlim &&
-                                      (long long)dx * dx + (long long)dy * dy + (long long)dz * dz < R &&
-                                      !(mi.x >= 0 && mi.x == mj.x);
-                            if (ok && (mi.y | mj.y))  // extra partner lists
-                                ok = !excluded_meta(ui.w, mi, s_e[wib][si], uj.w, mj, ej);
-                            lbyte |= (unsigned)ok << ic;
-                        }
+                        const unsigned lbyte =
+                            self0 ? tile_masks<true>(s_u[wib], cand, ia, jc * JC + jb, ujx, ujy, ujz, uj.w, R, d, gS, gT)
+                                  : tile_masks<false>(s_u[wib], cand, ia, jc * JC + jb, ujx, ujy, ujz, uj.w, R, d, gS, gT);
                         const unsigned imask = __reduce_or_sync(0xffffffffu, lbyte);
                         if (imask) {
                             if (nent < d.sub_cap) {
