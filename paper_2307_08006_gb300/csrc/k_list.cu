@@ -531,82 +531,99 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
             const int t0 = d.col_sc[W.col_off + col], tn = d.col_nsc[W.col_off + col];
             int nent = 0;
             const size_t ebase = sub * d.sub_cap;
-            for (int T_loc = t0; T_loc < t0 + tn && T_loc < nsc; ++T_loc) {
-                // cyclic half list over super-clusters: T is S's partner when it
-                // lies less than half-way round the index circle
-                if (T_loc != S_loc) {
-                    const int del = T_loc > S_loc ? T_loc - S_loc : T_loc - S_loc + nsc;
-                    if (2 * del > nsc || (2 * del == nsc && T_loc < S_loc)) continue;
-                }
-                const int t = W.sc_off + T_loc;
-                const int4 tlo = d.bb_sc[2 * (size_t)t], thi = d.bb_sc[2 * (size_t)t + 1];
-                if (tlo.w == 0) continue;
-                unsigned zpass = 0;  // z shifts whose super-cluster boxes are in range
-                for (int tz = -1; tz <= 1; ++tz) {
-                    if (T_loc == S_loc && (tx < 0 || (tx == 0 && (ty < 0 || (ty == 0 && tz < 0))))) continue;
-                    if (bb_dist2(slo, shi, tlo, thi, tx * U, ty * U, tz * U) < R) zpass |= 1u << (tz + 1);
-                }
-                if (!zpass) continue;
-                const int gT = W.slot_off + T_loc * SC;
-                __syncwarp();
-                for (int k = lane; k < SC; k += 32) {
-                    int4 u = d.uq[gT + k];
-                    const int2 m = d.smeta[gT + k];
-                    const int4 e = d.sexcl[gT + k];
-                    if (m.y || u.w < 0) u.x = u.y = u.z = FAR_J;
-                    u.w = slot_code(m, e, false);
-                    t_u[wib][k] = u;
-                }
-                t_bb[wib][lane] = d.bb_jc[2 * (size_t)t * NJC + lane];
-                __syncwarp();
-                for (int tz = -1; tz <= 1; ++tz) {
-                    if (!(zpass & (1u << (tz + 1)))) continue;
-                    const int shx = tx * U, shy = ty * U, shz = tz * U;
-                    const bool self0 = (T_loc == S_loc) && tx == 0 && ty == 0 && tz == 0;
-                    const int shift_bits = (tx + 1) | ((ty + 1) << 2) | ((tz + 1) << 4);
-                    // lane-parallel box tests of the 128 (jc, ic) combinations:
-                    // bit (jc & 3) * 8 + ic of word jc >> 2
-                    unsigned cm0, cm1, cm2, cm3;
-    #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int c = lane + 32 * q, jc = c >> 3, ic = c & 7;
-                        const int4 jlo = t_bb[wib][2 * jc], jhi = t_bb[wib][2 * jc + 1];
-                        const int4 ilo = s_bb[wib][2 * ic], ihi = s_bb[wib][2 * ic + 1];
-                        const bool ok = jlo.w > 0 && ilo.w > 0 && bb_dist2(ilo, ihi, jlo, jhi, shx, shy, shz) < R;
-                        const unsigned b = __ballot_sync(0xffffffffu, ok);
-                        if (q == 0) cm0 = b; else if (q == 1) cm1 = b; else if (q == 2) cm2 = b; else cm3 = b;
+            const int t_end = min(t0 + tn, nsc);
+            // the column's super-clusters 32 at a time: lane l tests T = tb + l
+            // (half-list rule, then its box against S's box for the three z
+            // shifts); the warp then visits the T with a shift in range in
+            // ascending order
+            for (int tb = t0; tb < t_end; tb += 32) {
+                unsigned zp_l = 0;  // z shifts whose super-cluster boxes are in range
+                {
+                    const int T_loc = tb + lane;
+                    bool partner = T_loc < t_end;
+                    // cyclic half list over super-clusters: T is S's partner when it
+                    // lies less than half-way round the index circle
+                    if (partner && T_loc != S_loc) {
+                        const int del = T_loc > S_loc ? T_loc - S_loc : T_loc - S_loc + nsc;
+                        partner = !(2 * del > nsc || (2 * del == nsc && T_loc < S_loc));
                     }
-                    // j-clusters with at least one candidate i-cluster, ascending
-                    unsigned jmask = 0;
-    #pragma unroll
-                    for (int t4 = 0; t4 < 4; ++t4) {
-                        jmask |= ((cm0 >> (8 * t4)) & 0xffu) ? 1u << t4 : 0u;
-                        jmask |= ((cm1 >> (8 * t4)) & 0xffu) ? 1u << (4 + t4) : 0u;
-                        jmask |= ((cm2 >> (8 * t4)) & 0xffu) ? 1u << (8 + t4) : 0u;
-                        jmask |= ((cm3 >> (8 * t4)) & 0xffu) ? 1u << (12 + t4) : 0u;
-                    }
-                    for (; jmask; jmask &= jmask - 1u) {
-                        const int jc = __ffs(jmask) - 1;
-                        const unsigned cw = jc < 8 ? (jc < 4 ? cm0 : cm1) : (jc < 12 ? cm2 : cm3);
-                        const unsigned cand = (cw >> ((jc & 3) * 8)) & 0xffu;
-                        const int4 uj = t_u[wib][jc * JC + jb];
-                        const int ujx = uj.x + shx, ujy = uj.y + shy, ujz = uj.z + shz;
-                        const unsigned lbyte =
-                            self0 ? tile_masks<true>(s_u[wib], cand, ia, jc * JC + jb, ujx, ujy, ujz, uj.w, R, d, gS, gT)
-                                  : tile_masks<false>(s_u[wib], cand, ia, jc * JC + jb, ujx, ujy, ujz, uj.w, R, d, gS, gT);
-                        const unsigned imask = __reduce_or_sync(0xffffffffu, lbyte);
-                        if (imask) {
-                            if (nent < d.sub_cap) {
-                                const size_t e = ebase + nent;
-                                // i-cluster mask twice: bits 8-15 are pruned by the batched
-                                // step, bits 16-23 keep the listed set
-                                if (lane == 0)
-                                    d.sub_hdr[e] = make_int2(gT + jc * JC, shift_bits | (int)(imask << 8) | (int)(imask << 16));
-                                d.sub_lb[32 * e + lane] = (unsigned char)lbyte;
-                            } else if (lane == 0) {
-                                set_status(d, LA_STATUS_LIST_OVERFLOW);
+                    if (partner) {
+                        const int t = W.sc_off + T_loc;
+                        const int4 tlo = d.bb_sc[2 * (size_t)t], thi = d.bb_sc[2 * (size_t)t + 1];
+                        if (tlo.w != 0) {
+                            for (int tz = -1; tz <= 1; ++tz) {
+                                if (T_loc == S_loc && (tx < 0 || (tx == 0 && (ty < 0 || (ty == 0 && tz < 0))))) continue;
+                                if (bb_dist2(slo, shi, tlo, thi, tx * U, ty * U, tz * U) < R) zp_l |= 1u << (tz + 1);
                             }
-                            ++nent;
+                        }
+                    }
+                }
+                for (unsigned tmask = __ballot_sync(0xffffffffu, zp_l != 0u); tmask; tmask &= tmask - 1u) {
+                    const int tl = __ffs(tmask) - 1;
+                    const int T_loc = tb + tl;
+                    const unsigned zpass = __shfl_sync(0xffffffffu, zp_l, tl);
+                    const int t = W.sc_off + T_loc;
+                    const int gT = W.slot_off + T_loc * SC;
+                    __syncwarp();
+                    for (int k = lane; k < SC; k += 32) {
+                        int4 u = d.uq[gT + k];
+                        const int2 m = d.smeta[gT + k];
+                        const int4 e = d.sexcl[gT + k];
+                        if (m.y || u.w < 0) u.x = u.y = u.z = FAR_J;
+                        u.w = slot_code(m, e, false);
+                        t_u[wib][k] = u;
+                    }
+                    t_bb[wib][lane] = d.bb_jc[2 * (size_t)t * NJC + lane];
+                    __syncwarp();
+                    for (int tz = -1; tz <= 1; ++tz) {
+                        if (!(zpass & (1u << (tz + 1)))) continue;
+                        const int shx = tx * U, shy = ty * U, shz = tz * U;
+                        const bool self0 = (T_loc == S_loc) && tx == 0 && ty == 0 && tz == 0;
+                        const int shift_bits = (tx + 1) | ((ty + 1) << 2) | ((tz + 1) << 4);
+                        // lane-parallel box tests of the 128 (jc, ic) combinations:
+                        // bit (jc & 3) * 8 + ic of word jc >> 2
+                        unsigned cm0, cm1, cm2, cm3;
+        #pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int c = lane + 32 * q, jc = c >> 3, ic = c & 7;
+                            const int4 jlo = t_bb[wib][2 * jc], jhi = t_bb[wib][2 * jc + 1];
+                            const int4 ilo = s_bb[wib][2 * ic], ihi = s_bb[wib][2 * ic + 1];
+                            const bool ok = jlo.w > 0 && ilo.w > 0 && bb_dist2(ilo, ihi, jlo, jhi, shx, shy, shz) < R;
+                            const unsigned b = __ballot_sync(0xffffffffu, ok);
+                            if (q == 0) cm0 = b; else if (q == 1) cm1 = b; else if (q == 2) cm2 = b; else cm3 = b;
+                        }
+                        // j-clusters with at least one candidate i-cluster, ascending
+                        unsigned jmask = 0;
+        #pragma unroll
+                        for (int t4 = 0; t4 < 4; ++t4) {
+                            jmask |= ((cm0 >> (8 * t4)) & 0xffu) ? 1u << t4 : 0u;
+                            jmask |= ((cm1 >> (8 * t4)) & 0xffu) ? 1u << (4 + t4) : 0u;
+                            jmask |= ((cm2 >> (8 * t4)) & 0xffu) ? 1u << (8 + t4) : 0u;
+                            jmask |= ((cm3 >> (8 * t4)) & 0xffu) ? 1u << (12 + t4) : 0u;
+                        }
+                        for (; jmask; jmask &= jmask - 1u) {
+                            const int jc = __ffs(jmask) - 1;
+                            const unsigned cw = jc < 8 ? (jc < 4 ? cm0 : cm1) : (jc < 12 ? cm2 : cm3);
+                            const unsigned cand = (cw >> ((jc & 3) * 8)) & 0xffu;
+                            const int4 uj = t_u[wib][jc * JC + jb];
+                            const int ujx = uj.x + shx, ujy = uj.y + shy, ujz = uj.z + shz;
+                            const unsigned lbyte =
+                                self0 ? tile_masks<true>(s_u[wib], cand, ia, jc * JC + jb, ujx, ujy, ujz, uj.w, R, d, gS, gT)
+                                      : tile_masks<false>(s_u[wib], cand, ia, jc * JC + jb, ujx, ujy, ujz, uj.w, R, d, gS, gT);
+                            const unsigned imask = __reduce_or_sync(0xffffffffu, lbyte);
+                            if (imask) {
+                                if (nent < d.sub_cap) {
+                                    const size_t e = ebase + nent;
+                                    // i-cluster mask twice: bits 8-15 are pruned by the batched
+                                    // step, bits 16-23 keep the listed set
+                                    if (lane == 0)
+                                        d.sub_hdr[e] = make_int2(gT + jc * JC, shift_bits | (int)(imask << 8) | (int)(imask << 16));
+                                    d.sub_lb[32 * e + lane] = (unsigned char)lbyte;
+                                } else if (lane == 0) {
+                                    set_status(d, LA_STATUS_LIST_OVERFLOW);
+                                }
+                                ++nent;
+                            }
                         }
                     }
                 }
