@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
                         // lane-parallel box tests of the 128 (jc, ic) combinations:
                         // bit (jc & 3) * 8 + ic of word jc >> 2
                         unsigned cm0, cm1, cm2, cm3;
-        #pragma unroll
+#pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int c = lane + 32 * q, jc = c >> 3, ic = c & 7;
                             const int4 jlo = t_bb[wib][2 * jc], jhi = t_bb[wib][2 * jc + 1];
@@ -593,14 +593,13 @@ __global__ void __launch_bounds__(LB_WARPS * 32, 8) k_listbuild(Dev d, int w0, i
                             if (q == 0) cm0 = b; else if (q == 1) cm1 = b; else if (q == 2) cm2 = b; else cm3 = b;
                         }
                         // j-clusters with at least one candidate i-cluster, ascending
-                        unsigned jmask = 0;
-        #pragma unroll
-                        for (int t4 = 0; t4 < 4; ++t4) {
-                            jmask |= ((cm0 >> (8 * t4)) & 0xffu) ? 1u << t4 : 0u;
-                            jmask |= ((cm1 >> (8 * t4)) & 0xffu) ? 1u << (4 + t4) : 0u;
-                            jmask |= ((cm2 >> (8 * t4)) & 0xffu) ? 1u << (8 + t4) : 0u;
-                            jmask |= ((cm3 >> (8 * t4)) & 0xffu) ? 1u << (12 + t4) : 0u;
-                        }
+                        // (a non-zero byte of a word -> one bit: the byte flags
+                        // 0x01 at bits 0, 8, 16, 24 times 0x01020408 land at
+                        // bits 24-27 without carries)
+                        const auto nib = [](unsigned w) {
+                            return ((__vcmpne4(w, 0u) & 0x01010101u) * 0x01020408u) >> 24;
+                        };
+                        unsigned jmask = nib(cm0) | (nib(cm1) << 4) | (nib(cm2) << 8) | (nib(cm3) << 12);
                         for (; jmask; jmask &= jmask - 1u) {
                             const int jc = __ffs(jmask) - 1;
                             const unsigned cw = jc < 8 ? (jc < 4 ? cm0 : cm1) : (jc < 12 ? cm2 : cm3);
