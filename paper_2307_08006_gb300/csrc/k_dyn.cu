@@ -107,8 +107,11 @@ __global__ void k_integrate(Dev d, int w0, int w1, int g0, int g1) {
         float dz = min_image(x.z - r.z, S.boxf, S.box_invf);
         // all walkers of the system rebuild together: their rebuild kernels
         // then run once, fully parallel, instead of on most steps
-        if (dx * dx + dy * dy + dz * dz > S.half_skin2)
+        const float disp2 = dx * dx + dy * dy + dz * dz;
+        if (disp2 > S.half_skin2)
             for (int k = 0; k < S.w_count; ++k) d.rebuild[S.w_first + k] = 1;
+        else if (disp2 > S.near_skin2)
+            for (int k = 0; k < S.w_count; ++k) d.near[S.w_first + k] = 1;
         // the same for the pruned tiles of the batched step; all walkers of the
         // system re-prune together, so that a pair launch runs either the
         // pruning form of the item loop or the common one.  The positions this

@@ -857,6 +857,7 @@ __global__ void k_items(Dev d, int w0, int prune_fresh) {
         if (carry > W.item_cap) set_status(d, LA_STATUS_LIST_OVERFLOW);
         d.n_items[w] = min(carry, W.item_cap);
         d.rebuild[w] = 0;
+        d.near[w] = 0;
         if (prune_fresh && d.sys[W.sys].prune_disp2 > 0.f) d.prune_now[w] = d.step[w] + 1ull;
         atomicAdd(&d.counters[0], 1ull);
     }
@@ -866,10 +867,18 @@ __global__ void k_items(Dev d, int w0, int prune_fresh) {
 // gate of the batched step, after the integrator: a walker whose pruning was
 // requested is re-pruned by this step's pair pass (prune_now = 1 + step
 // counter; the next integrator step takes the positions it starts from as the
-// walker's new reference).  Inside a CUDA graph one thread also sets the
-// step's conditional handle to "some walker must rebuild", so that the graph
-// skips the list kernels otherwise; such steps are counted in counters[6].
+// walker's new reference).  When some walker must rebuild, the walkers whose
+// systems are due soon (near flags) join it (coalescing).  Inside a CUDA
+// graph one thread also sets the step's conditional handle to "some walker
+// must rebuild", so that the graph skips the list kernels otherwise; such
+// steps are counted in counters[6].
 // -------------------------------------------------------------------------
+__device__ __forceinline__ void coalesce_rebuilds(const Dev &d, int w0, int w1, int any) {
+    if (!any) return;
+    for (int w = w0 + threadIdx.x; w < w1; w += blockDim.x)
+        if (d.near[w]) d.rebuild[w] = 1;
+}
+
 __global__ void k_gate(Dev d, int w0, int w1, cudaGraphConditionalHandle handle, int conditional) {
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
@@ -884,6 +893,7 @@ __global__ void k_gate(Dev d, int w0, int w1, cudaGraphConditionalHandle handle,
         if (d.rebuild[w]) any = 1;
     }
     __syncthreads();
+    coalesce_rebuilds(d, w0, w1, any);
     if (conditional && threadIdx.x == 0) {
         cudaGraphSetConditional(handle, any ? 1u : 0u);
         if (any) atomicAdd(&d.counters[6], 1ull);
@@ -894,6 +904,19 @@ void launch_gate(const Dev &d, int w0, int w1, cudaGraphConditionalHandle handle
                  cudaStream_t s) {
     k_gate<<<1, 256, 0, s>>>(d, w0, w1, handle, conditional ? 1 : 0);
 }
+
+// the one-walker-per-launch form's coalescing (no pruning there)
+__global__ void k_coalesce(Dev d, int w0, int w1) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int w = w0 + threadIdx.x; w < w1; w += blockDim.x)
+        if (d.rebuild[w]) any = 1;
+    __syncthreads();
+    coalesce_rebuilds(d, w0, w1, any);
+}
+
+void launch_coalesce(const Dev &d, int w0, int w1, cudaStream_t s) { k_coalesce<<<1, 256, 0, s>>>(d, w0, w1); }
 
 // -------------------------------------------------------------------------
 // host launcher of the whole rebuild chain (every kernel exits early for

@@ -303,6 +303,7 @@ size_t carve(const Layout &L, char *base, size_t cap, Dev &d, void **io, int *io
     d.pending = a.take<int>(L.W);
     d.rebuild = a.take<int>(L.W);
     d.prune = a.take<int>(L.W);
+    d.near = a.take<int>(L.W);
     d.prune_now = a.take<unsigned long long>(L.W);
     d.eterm = a.take<long long>((size_t)L.W * N_ETERMS);
     d.abf_sum = a.take<double>(L.total_bins);
@@ -792,6 +793,7 @@ int la_create_system(const la_system_desc *sys, int n_sys, const la_options *opt
         D.sd_lm = std::sqrt(std::max(0.0, (1.0 - D.c_lm * D.c_lm) * S.m_lambda * S.kT));
         D.kT = S.kT;
         D.half_skin2 = (float)(0.25 * S.skin * S.skin);
+        D.near_skin2 = (float)(0.25 * S.skin * S.skin * NEAR_FRACTION * NEAR_FRACTION);
         {
             const double pm = h->opt.prune_margin;
             const bool on = pm > 0.0 && pm < S.skin;
@@ -1069,6 +1071,8 @@ int la_step_walkers_plain(la_handle *h, int64_t n_steps, void *stream) {
         // every walker's integrator runs before any rebuild: a walker that
         // moves too far flags all walkers of its system for this step
         for (int w = 0; w < W; ++w) launch_integrate(h->d, h->hv, w, w + 1, s);
+        launch_coalesce(h->d, 0, W, s);  // the batched step's gate does the same
+        h->launches += 1;
         for (int w = 0; w < W; ++w) {
             launch_rebuild(h->d, h->hv, w, w + 1, s);
             launch_pairs(h->d, h->hv, w, w + 1, false, s);

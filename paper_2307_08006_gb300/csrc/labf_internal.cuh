@@ -51,6 +51,7 @@ struct SysDev {
     float dt, c_at, s_at;         // atoms: dt, exp(-gamma dt), sqrt(1 - c^2)
     double dt_d, m_lambda, c_lm, sd_lm, kT;  // lambda particle
     float half_skin2;             // (skin / 2)^2
+    float near_skin2;             // (NEAR_FRACTION skin / 2)^2: "due soon" for coalescing
     float prune_disp2;            // squared displacement that triggers pruning (0: off)
     float rprune2;                // (r_c + prune margin)^2
     long long R;                  // integer list threshold
@@ -168,6 +169,7 @@ struct Dev {
     unsigned int *wdone, *sdone;  // arrivals per walker / per stage in the fused pair launch
     float4 *xprune;               // positions at the last pruning, per slot
     int *prune;                   // per walker: pruning requested (displacement or fresh list)
+    int *near;                    // per walker: an atom of its system moved NEAR_FRACTION skin/2
     unsigned long long *prune_now;  // per walker: 0, or 1 + the step counter of the batched
                                     // step whose pair pass re-prunes the walker's tiles
     unsigned long long *counters; // [0] rebuilds [1] pairs normal [2] pairs alch [4, 5] pair
@@ -178,6 +180,12 @@ struct Dev {
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
+// Rebuild coalescing: a system whose atoms have moved NEAR_FRACTION of the
+// rebuild threshold rebuilds together with any other system that must
+// rebuild in the same step, so that batches of several systems share list
+// builds instead of paying one chain of list kernels each.
+constexpr float NEAR_FRACTION = 0.8f;
+
 __device__ __forceinline__ void set_status(const Dev &d, unsigned bits) { atomicOr(d.status, bits); }
 
 // Debug builds (nvcc -DLA_CHECKS=1; build(checks=True) in the package's

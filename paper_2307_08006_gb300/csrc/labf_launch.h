@@ -27,6 +27,9 @@ void launch_items(const Dev &d, const HostView &hv, int w0, int w1, cudaStream_t
 void launch_gate(const Dev &d, int w0, int w1, cudaGraphConditionalHandle handle, bool conditional,
                  cudaStream_t s);
 int rebuild_kernel_count(const HostView &hv, int w0, int w1);
+// rebuild coalescing of the one-walker-per-launch form (the batched step's
+// gate does the same)
+void launch_coalesce(const Dev &d, int w0, int w1, cudaStream_t s);
 void launch_pairs(const Dev &d, const HostView &hv, int w0, int w1, bool energy, cudaStream_t s);
 // pairs + bonded + walker terms + lambda update of all walkers in one launch
 void launch_pairs_fused(const Dev &d, const HostView &hv, int n_stages, cudaStream_t s);
