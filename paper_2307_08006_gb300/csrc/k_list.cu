@@ -708,10 +708,14 @@ __global__ void __launch_bounds__(128) k_listcompact(Dev d, int w0, int w1) {
 constexpr int AL_WARPS = 4;
 
 __global__ void __launch_bounds__(AL_WARPS * 32) k_alchlist(Dev d, int w0, int w1, int a0, int a1) {
-    // one block per (walker, alchemical atom); the near super-clusters of
-    // each chunk of 32 are tested by the block's warps in turn, and warp 0
-    // writes the hits in (super-cluster, slot) order
-    __shared__ unsigned long long okm[32];
+    // one block per (walker, alchemical atom); the super-clusters are box
+    // tested one per thread, 128 per round, the near ones compacted in
+    // ascending order and tested slot by slot by the block's warps in turn,
+    // and warp 0 writes the hits in (super-cluster, slot) order
+    constexpr int NT = AL_WARPS * 32;
+    __shared__ unsigned long long okm[NT];
+    __shared__ int near_sc[NT];
+    __shared__ int wcnt[AL_WARPS];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     for (int it = a0 + blockIdx.x; it < a1; it += gridDim.x) {
         int lo = w0, hi = w1 - 1;
@@ -735,11 +739,11 @@ __global__ void __launch_bounds__(AL_WARPS * 32) k_alchlist(Dev d, int w0, int w
         int cnt = 0;
         const int nsc = d.n_sc[w];
         int *out = d.alch_slot + (size_t)it * d.alch_cap;
-        for (int b0 = 0; b0 < nsc; b0 += 32) {
+        for (int b0 = 0; b0 < nsc; b0 += NT) {
             // super-cluster box within the list radius of the atom (any image)
             bool near = false;
-            if (b0 + lane < nsc) {
-                const size_t t = (size_t)(W.sc_off + b0 + lane);
+            if (b0 + (int)threadIdx.x < nsc) {
+                const size_t t = (size_t)(W.sc_off + b0 + threadIdx.x);
                 const int4 tlo = d.bb_sc[2 * t], thi = d.bb_sc[2 * t + 1];
                 if (tlo.w > 0) {
                     long long D = 0;
@@ -756,11 +760,19 @@ __global__ void __launch_bounds__(AL_WARPS * 32) k_alchlist(Dev d, int w0, int w
                     near = D < S.R;
                 }
             }
+            // compaction in ascending order: warp counts, then offsets
             const unsigned nm = __ballot_sync(0xffffffffu, near);
-            int kk = 0;
-            for (unsigned m = nm; m; m &= m - 1u, ++kk) {
-                if ((kk % AL_WARPS) != wib) continue;
-                const int gbase = W.slot_off + (b0 + __ffs(m) - 1) * SC;
+            if (lane == 0) wcnt[wib] = __popc(nm);
+            __syncthreads();
+            int off = 0, nn = 0;
+            for (int q = 0; q < AL_WARPS; ++q) {
+                off += q < wib ? wcnt[q] : 0;
+                nn += wcnt[q];
+            }
+            if (near) near_sc[off + __popc(nm & ((1u << lane) - 1u))] = b0 + threadIdx.x;
+            __syncthreads();
+            for (int kk = wib; kk < nn; kk += AL_WARPS) {
+                const int gbase = W.slot_off + near_sc[kk] * SC;
                 unsigned bits[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -779,9 +791,8 @@ __global__ void __launch_bounds__(AL_WARPS * 32) k_alchlist(Dev d, int w0, int w
             }
             __syncthreads();
             if (wib == 0) {
-                kk = 0;
-                for (unsigned m = nm; m; m &= m - 1u, ++kk) {
-                    const int gbase = W.slot_off + (b0 + __ffs(m) - 1) * SC;
+                for (int kk = 0; kk < nn; ++kk) {
+                    const int gbase = W.slot_off + near_sc[kk] * SC;
                     const unsigned long long om = okm[kk];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
