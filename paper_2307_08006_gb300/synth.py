@@ -192,7 +192,8 @@ def _water_molecule(origin: np.ndarray) -> np.ndarray:
 
 def _solute_params(rng, n_sol: int):
     q = rng.normal(0.0, 0.3, n_sol)
-    q -= q.mean()
+    if n_sol > 0:
+        q -= q.mean()
     sig = rng.uniform(0.3, 0.4, n_sol)
     eps = rng.uniform(0.2, 0.6, n_sol)
     return q, sig, eps

@@ -388,3 +388,32 @@ def test_single_atom_system_and_rebuilds():
         s = eng.get_state(w)
         assert np.abs(s["x"] - sim.a["x"][w]).max() < 1e-3
         assert s["lam"] == pytest.approx(sim.a["lam"][w], abs=1e-4)
+
+
+def test_system_without_alchemical_atoms():
+    """Degenerate case: no alchemical atom (pure water).  dU/dlambda is 0 for
+    every walker, every force and energy term and the pair set still match the
+    oracle, the ABF bins collect exact zeros, and the batched and plain forms
+    agree bit for bit."""
+    sp = small_water(n_w=120, n_s=0, box=1.6, seed=9, jitter=0.02)
+    assert int(sp.alch.sum()) == 0
+    run = synth.water_run(walkers_per_stage=2, n_bins=10)
+    st = synth.initial_state(sp, run, lam0=[0.2, 0.4, 0.6, 0.8])
+    e1, _ = make_engine(sp, run, state=st, graph_steps=4)
+    for w in range(run.n_walkers):
+        g, ref = check_forces(e1, sp, st, w)
+        assert g["dUdl"] == 0.0 and ref["dUdl"] == 0.0
+    osys = oracle.OracleSystem(sp)
+    pairs, kind = e1.get_pairs(0)
+    opairs, okind = oracle.pair_set(osys, st.x[0], sp.r_cut + run.skin)
+    assert len(pairs) > 0 and np.array_equal(pairs, opairs) and np.array_equal(kind, okind)
+    e2, _ = make_engine(sp, run, state=st, graph_steps=4)
+    e1.step(30)
+    e2.step_plain(30)
+    for w in range(run.n_walkers):
+        a, b = e1.get_state(w), e2.get_state(w)
+        assert np.array_equal(a["x"], b["x"]) and a["lam"] == b["lam"]
+    for stage in range(2):
+        r = e1.read_abf(0, stage)
+        assert int(r["count"].sum()) == 2 * 30
+        assert np.all(r["sum"] == 0.0) and np.all(r["sumsq"] == 0.0)
