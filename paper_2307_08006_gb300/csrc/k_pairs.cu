@@ -37,6 +37,16 @@
 namespace labf {
 
 constexpr int EPC = 32;  // entries prepared per pass (one per lane)
+
+// x^n for an integer n >= 0 (square and multiply; exact for n <= 1)
+__device__ __forceinline__ double ipow(double x, int n) {
+    double r = 1.0;
+    for (; n > 0; n >>= 1) {
+        if (n & 1) r *= x;
+        x *= x;
+    }
+    return r;
+}
 constexpr unsigned FULL = 0xffffffffu;
 
 template <int WARPS>
@@ -384,11 +394,14 @@ __device__ __forceinline__ void alch_items(const Dev &d, int w0, int w1, int a0,
         double lvd, led, dlvd, dled;
         lambda_path(d.lam[w], S.b_v, S.b_e, lvd, led, dlvd, dled);
         const float le = (float)led;
-        const float lvn = (float)pow(lvd, (double)S.sc_n);
-        const float dlvn = (float)((double)S.sc_n * pow(lvd, (double)(S.sc_n - 1)));
-        const float sa = (float)((double)S.sc_alpha * pow(1.0 - lvd, (double)S.sc_m));
-        const float dsdl = (float)(-(double)S.sc_m * S.sc_alpha * pow(1.0 - lvd, (double)(S.sc_m - 1)));
+        // integer soft-core powers by repeated multiplication: the FP64 pipe
+        // is narrow on this GPU, and the warps of a block share one SM's
+        const float lvn = (float)ipow(lvd, S.sc_n);
+        const float dlvn = (float)((double)S.sc_n * ipow(lvd, S.sc_n - 1));
+        const float sa = (float)((double)S.sc_alpha * ipow(1.0 - lvd, S.sc_m));
+        const float dsdl = (float)(-(double)S.sc_m * S.sc_alpha * ipow(1.0 - lvd, S.sc_m - 1));
         const float eps_a = 0.25f * la.y * la.y;
+        const double inv2eps = 0.5 / (double)eps_a;  // d e4 / d eps_a = e4 / (2 eps_a)
         const float rc2 = S.rc2, krf = S.krf, crf = S.crf;
         float fax = 0.f, fay = 0.f, faz = 0.f;
         double sv = 0.0, se = 0.0, usc_s = 0.0, urf_s = 0.0;
@@ -439,8 +452,8 @@ __device__ __forceinline__ void alch_items(const Dev &d, int w0, int w1, int a0,
             urf_s += (double)(le * rf_u);
             if (S.theta_stats || ENERGY) {
                 if (e4 > 0.f) {
-                    th0 += (double)usc / (2.0 * (double)eps_a);
-                    th3 += (double)dsc / (2.0 * (double)eps_a);
+                    th0 += (double)usc * inv2eps;
+                    th3 += (double)dsc * inv2eps;
                     const float ds_dsig = -6.0f * rho6 / sg;
                     th1 += 0.5 * (double)(lvn * e4 * g1 * ds_dsig);
                     th4 += 0.5 * (double)(dlvn * e4 * g1 * ds_dsig + lvn * e4 * g2 * ds_dsig * dsdl);
